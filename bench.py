@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the deep-octree ray caster on GB300: Mrays/s and stereo frames/s.
+
+Workload (default): the depth-24 canvas of 40 km (finest cell 2.4 mm) built
+from 210,000 seeded sphere stamps, rendered as a stereo pair of 2160 x 2160
+per eye from inside a 1 m room (synth config 2). One step = one render of
+both eyes through the C ABI (one persistent launch of the mixed-precision
+kernel). The canvas is resident in HBM before timing; L2 is flushed (256 MB
+write) before every timed step, and each step is timed with CUDA events on
+the launching stream.
+
+Also reported: the plain FP64 GPU path (one launch per view) on the same
+views, the max abs error against the FP64 oracle on a seeded pixel sample,
+the end-to-end rate through canvox_render_host (view table up, image down),
+the roofline of the traversal kernel and the oracle timed on the host cores.
+
+  python bench.py [--gpus N --steps K --warmup W --impl {canvox,reference} --config C]
+Under torchrun each rank renders its own copy of the workload (replicas:
+weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s and stereo frames/s at depth 24-27 vs plain FP64 GPU path; max err vs FP64"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["canvox", "reference"], default="canvox")
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 baseline, e2e and CPU baseline")
+    ap.add_argument("--opts", type=str, default="", help="render options as JSON")
+    return ap.parse_args()
+
+
+def workload_name(cid):
+    import synth
+    return synth.CONFIGS[cid]["name"]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the traversal kernel from the committed ncu summary (or None)."""
+    p = os.path.join(ROOT, "profiles", "mixed_kernel_c2_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":", 1)[1])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_rate(canvas, cams, budget_s, seed=12345):
+    """Time the FP64 oracle on a seeded pixel sample sized for ~budget_s on all host cores."""
+    import oracle
+    import synth
+    total = synth.total_pixels(cams)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(total).astype(np.int64)
+    n, spent, done, out = 256, 0.0, 0, []
+    t_start = time.perf_counter()
+    while done < total:
+        px = order[done:done + n]
+        t = time.perf_counter()
+        out.append((px, oracle.render(canvas, cams, px_idx=px)))
+        dt = time.perf_counter() - t
+        spent += dt
+        done += len(px)
+        if spent >= budget_s:
+            break
+        rate = len(px) / max(dt, 1e-9)
+        n = int(min(max(256, rate * (budget_s - spent) * 0.5), 1 << 20))
+    wall = time.perf_counter() - t_start
+    px = np.concatenate([p for p, _ in out])
+    ref = np.concatenate([r for _, r in out])
+    return px, ref, done / wall / 1e6, wall, oracle.max_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    cid = args.config
+    canvas = synth.build_config(cid)
+    cams = synth.config_cameras(cid)
+    import oracle
+    total = synth.total_pixels(cams)
+    rng = np.random.default_rng(777)
+    # each step: a bounded sample of the workload, sized so that warmup + steps end within minutes
+    probe = rng.choice(total, size=512, replace=False).astype(np.int64)
+    t = time.perf_counter()
+    oracle.render(canvas, cams, px_idx=probe)
+    rate = 512 / max(time.perf_counter() - t, 1e-6)
+    per_step = int(max(256, min(total, rate * 120.0 / max(1, args.steps + args.warmup))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        px = rng.choice(total, size=per_step, replace=False).astype(np.int64)
+        t = time.perf_counter()
+        oracle.render(canvas, cams, px_idx=px)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    sec = sum(times) / len(times)
+    value = per_step / sec / 1e6
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
+        "config": {"workload": workload_name(cid), "rays_per_frame": total, "step_sample_rays": per_step},
+        "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} seeded random pixels of the {total}-ray frame per step"},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1704_02724_gb300 as cx
+    import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cid = args.config
+    opts = json.loads(args.opts) if args.opts else {}
+    canvas = synth.build_config(cid)
+    cams = synth.config_cameras(cid)
+    n_px = synth.total_pixels(cams)
+    cx.upload_octree(canvas.nodes, canvas.leaves, canvas.depth, canvas.extent)
+    h_hash, d_hash = cx.octree_hash()
+    out = torch.empty((n_px, 4), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        cx.render(cams, out, **opts)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        cx.render(cams, out, **opts)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = sum(ms) / len(ms)
+    stats = cx.get_stats(check=False)
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    rays = stats["rays"]
+    value = world * rays / (ms_max * 1e-3) / 1e6
+
+    line = None
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        algo_bytes = 32 * stats["slot_reads"] + 8 * stats["leaf_loads"] + 16 * stats["rays"]
+        achieved = algo_bytes / (ms_step * 1e-3) / 1e9
+        traffic = profiled_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
+            "config": {"workload": workload_name(cid) + f" ({len(cams)} views, {n_px} rays, depth {canvas.depth},"
+                       f" {canvas.n_records} records, {canvas.n_leaves} leaves)",
+                       "rays_per_step": rays * world, "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": f"replicas x{world}", "opts": cx.default_opts() | opts},
+            "stereo_fps": (world / (ms_max * 1e-3)) if len(cams) == 2 else None,
+            "wall_ms_per_step_incl_flush": wall * 1e3 / args.steps,
+            "gpu_launches": args.steps * (1 if not opts.get("per_view") else len(cams)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": algo_bytes,
+                         "bytes_formula": "32*slot_reads + 8*leaf_loads + 16*rays"},
+            "stats": {k: v for k, v in stats.items() if k != "status"},
+            "hash_ok": h_hash == d_hash,
+            "clocks": clk,
+        }
+    if rank == 0 and not args.no_extras and world == 1:
+        # plain FP64 GPU path on the same views (one launch per view)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out64 = torch.empty_like(out)
+        cx.render(cams, out64, precision=cx.PREC_FP64)
+        torch.cuda.synchronize()
+        f64 = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            cx.render(cams, out64, precision=cx.PREC_FP64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f64.append(e0.elapsed_time(e1))
+        ms64 = statistics.median(f64)
+        line["fp64_plain"] = {"value": rays / (ms64 * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms64,
+                              "speedup_of_mixed": ms64 / ms_step}
+        out32 = torch.empty_like(out)
+        cx.render(cams, out32, precision=cx.PREC_FP32)
+        torch.cuda.synchronize()
+        # end to end through canvox_render_host: view table up, image down, every step
+        host = torch.empty((n_px, 4), dtype=torch.float32, pin_memory=True)
+        cx.render_host(cams, host, **opts)
+        k_e2e = min(args.steps, 10)
+        t = time.perf_counter()
+        for _ in range(k_e2e):
+            cx.render_host(cams, host, **opts)
+        e2e_s = (time.perf_counter() - t) / k_e2e
+        st2 = cx.get_stats(check=False)
+        line["e2e"] = {"value": rays / e2e_s / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": st2["h2d_bytes"],
+                       "d2h_bytes_per_step": st2["d2h_bytes"], "ms_per_step": e2e_s * 1e3}
+        # FP64 oracle on host cores: CPU baseline and the error of each GPU path on its sample
+        px, ref, rate, wall_s, cores = oracle_rate(canvas, cams, args.cpu_seconds)
+        img = out.cpu().numpy().astype(np.float64)[px]
+        err = np.abs(img - ref).max(axis=1)
+        line["cpu_baseline"] = {"value": rate, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{len(px)} seeded random pixels of the {n_px}-ray frame, {wall_s:.1f} s"}
+        line["max_err_vs_oracle"] = {
+            "mixed": float(err.max()), "mixed_pixels_over_1e-5": int(np.sum(err > 1e-5)),
+            "fp64_plain": float(np.abs(out64.cpu().numpy().astype(np.float64)[px] - ref).max()),
+            "fp32_plain": float(np.abs(out32.cpu().numpy().astype(np.float64)[px] - ref).max()),
+            "pixels": int(len(px))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * canvox.h - C ABI of the GB300 deep-octree ray caster (libcanvox.so).
+ *
+ * The library renders a canvas stored as a deep sparse octree (depth 1..30)
+ * by casting one ray per pixel, compositing the leaves' colour and extinction
+ * front to back and stopping early at full opacity (the rendering problem of
+ * Sec. 6 of "CanvoX: High-resolution VR Painting in Large Volumetric Canvas",
+ * arXiv 1704.02724). All entry points are plain C: host or device pointers,
+ * sizes and small structs; no C++ or PyTorch types cross this boundary.
+ *
+ * Threading and ownership: one global library context per process, bound to
+ * the CUDA device that is current at canvox_upload_octree. Calls are not
+ * thread-safe; serialise them. The library owns its device copy of the octree,
+ * its camera staging buffers and its statistics buffer. The caller owns every
+ * output buffer and every stream passed in.
+ *
+ * Errors: every int-returning call returns CANVOX_OK (0) or a negative
+ * CANVOX_ERR_* code and sets a message readable with canvox_last_error().
+ * No call aborts, throws or traps.
+ */
+#ifndef CANVOX_H
+#define CANVOX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CANVOX_OK 0
+#define CANVOX_ERR_INVALID_ARG (-1) /* bad pointer, size or option; nothing was launched */
+#define CANVOX_ERR_NOT_UPLOADED (-2) /* render or hash before a successful upload */
+#define CANVOX_ERR_BAD_TREE (-3)     /* upload validation failed; the previous canvas is kept */
+#define CANVOX_ERR_CUDA (-4)         /* a CUDA runtime call failed (message has the CUDA error) */
+#define CANVOX_ERR_OOM (-5)          /* device or pinned host allocation failed */
+#define CANVOX_ERR_STEP_LIMIT (-6)   /* some ray hit the per-ray step limit (partial pixel written) */
+
+#define CANVOX_PREC_MIXED 0 /* FP32 cell-local frames, FP64 rebase and error-budgeted FP64 boundaries */
+#define CANVOX_PREC_FP64 1  /* plain FP64: canvas coordinates, leaf located from the root each step */
+#define CANVOX_PREC_FP32 2  /* plain FP32 in canvas coordinates (the failing baseline of Sec. 6.3) */
+
+/*
+ * One view (Sec. 6.1: the eye position is kept in FP64 canvas coordinates so
+ * that stereo eyes do not snap to FP32 values). 136 bytes, no padding.
+ *   eye, right, up, forward : canvas coordinates; right/up/forward need not be
+ *       exactly orthonormal: the library orthonormalises them by Gram-Schmidt
+ *       starting from forward, then up, then right.
+ *   tan_half_fov_y : tangent of half the vertical field of view (> 0).
+ *   width, height  : image size in pixels (>= 1 each).
+ *   out_offset_px  : index of this view's pixel (0,0) in the output image;
+ *       pixel (i, j) (column i, row j from the top) is written at
+ *       out_offset_px + j * width + i. Views must not overlap.
+ *   background     : RGBA behind the canvas; the output is
+ *       (C + T bg.rgb, 1 - T) with T the transmittance left at the end.
+ * Pixel (i, j) shoots the ray through its centre:
+ *   d = normalize(f + u r + v up), u = (2(i+1/2)/W - 1) tan * W/H,
+ *   v = (1 - 2(j+1/2)/H) tan.
+ */
+typedef struct canvox_camera {
+    double eye[3];
+    double right[3];
+    double up[3];
+    double forward[3];
+    double tan_half_fov_y;
+    int32_t width;
+    int32_t height;
+    int64_t out_offset_px;
+    float background[4];
+} canvox_camera;
+
+/*
+ * Render options. Fill with canvox_default_opts() and change what you need.
+ *   precision     : CANVOX_PREC_*.
+ *   per_view      : 0 = all views in one persistent launch; 1 = one launch per view.
+ *   use_graph     : 1 = replay the launch sequence from a cached CUDA graph.
+ *   block_threads : threads per block of the persistent kernel (multiple of 32, 32..256).
+ *   blocks_per_sm : persistent blocks per SM (the grid is SMs x this).
+ *   refill        : a warp refetches rays when at most this many lanes are still busy (0..31).
+ *   smem_records  : records of the breadth-first tree prefix kept in shared memory (0 = none).
+ *   frame_levels  : K, the most levels a local FP32 frame may sit above its cell (1..22).
+ *   step_limit    : most leaves one ray may visit (0 = 3 * 2^depth + 8, capped at 2^31 - 1).
+ *   t_min         : stop a ray once its transmittance is below this (< 0: default 2^-20).
+ *   err_budget    : per-ray bound on the colour error the FP32 boundaries may add before
+ *                   the remaining boundaries are taken in FP64 (mixed precision only).
+ *   step_count    : optional device int32 per output pixel: leaves visited by its ray.
+ */
+typedef struct canvox_render_opts {
+    int32_t precision;
+    int32_t per_view;
+    int32_t use_graph;
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t refill;
+    int32_t smem_records;
+    int32_t frame_levels;
+    int64_t step_limit;
+    float t_min;
+    float err_budget;
+    int32_t* step_count;
+} canvox_render_opts;
+
+/* Counters of the last completed render call (sums over all its rays). */
+typedef struct canvox_stats {
+    int64_t rays;            /* rays traced (pixels) */
+    int64_t steps;           /* leaves visited */
+    int64_t slot_reads;      /* child-slot reads a perfect stack needs: levels re-descended from the LCA */
+    int64_t leaf_loads;      /* non-empty leaf values read (8 B each) */
+    int64_t record_loads;    /* child-slot loads actually issued (stack restarts included) */
+    int64_t fp64_boundaries; /* leaf boundaries whose crossing time was taken in FP64 */
+    int64_t rebases;         /* local frames entered (FP64 rebase of the ray) */
+    int64_t step_limited;    /* rays stopped by the step limit */
+    int64_t h2d_bytes;       /* host-to-device bytes the call copied (view table) */
+    int64_t d2h_bytes;       /* device-to-host bytes the call copied (image, canvox_render_host only) */
+} canvox_stats;
+
+/* Fill *o with the defaults (tuned values once canvox_autotune has run). */
+void canvox_default_opts(canvox_render_opts* o);
+
+/*
+ * Validate and copy a canvas to the current CUDA device (synchronous).
+ *   node_pool  : host int32[n_records][8], record 0 = root cell [-E/2, E/2]^3.
+ *                Slot k of record r is child k = x + 2y + 4z (x, y, z = high
+ *                half on that axis; Sec. 4.1.1: eight children per allocation
+ *                unit, consecutive indices): v > 0 index of the child's record,
+ *                v == 0 empty leaf (extinction 0), v < 0 leaf index -v-1.
+ *   leaf_rgba  : host uint16[n_leaves][4], IEEE FP16 bits (R, G, B, sigma); sigma is
+ *                the extinction per canvas unit (finite, >= 0); R, G, B finite.
+ *   depth      : deepest level allowed (1..30); the finest cell is extent * 2^-depth.
+ *   extent     : canvas side (> 0, finite, at most 23 significant bits so that
+ *                every cell plane is exact in FP64).
+ * Validation (CANVOX_ERR_BAD_TREE on failure, previous canvas kept): internal
+ * children numbered 1, 2, ... in breadth-first order (each referenced once,
+ * no cycles), leaves numbered 0, 1, ... in the same order, no record deeper
+ * than depth - 1, leaf values finite with sigma >= 0. The host pools may be
+ * freed on return. A 64-bit hash of the device copy is checked against the
+ * host pools before the call returns.
+ */
+int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint16_t* leaf_rgba,
+                         int64_t n_leaves, int32_t depth, double extent);
+
+/*
+ * Render n_views views into out_rgba_dev (device float32 RGBA, at least
+ * max(out_offset_px + width * height) pixels, 16 bytes each), stream-ordered
+ * on `stream` (a cudaStream_t; NULL = legacy default stream) with the default
+ * options. Asynchronous: returns after enqueueing. `cams` is host memory and
+ * may be freed on return. n_views == 0 is a no-op.
+ */
+int canvox_render(const canvox_camera* cams, int32_t n_views, float* out_rgba_dev, void* stream);
+
+/* canvox_render with explicit options (opts == NULL: defaults). */
+int canvox_render_ex(const canvox_camera* cams, int32_t n_views, float* out_rgba_dev, void* stream,
+                     const canvox_render_opts* opts);
+
+/*
+ * Render into host memory: the image is produced in a library-owned device
+ * buffer and copied to out_rgba_host (float32 RGBA, max(out_offset_px + W*H)
+ * pixels; pinned memory copies fastest). Synchronous: returns when the host
+ * buffer holds the image.
+ */
+int canvox_render_host(const canvox_camera* cams, int32_t n_views, float* out_rgba_host, void* stream,
+                       const canvox_render_opts* opts);
+
+/* Counters of the last render (synchronises with the library's work). */
+int canvox_get_stats(canvox_stats* s);
+
+/* 64-bit hashes of the uploaded pools: recomputed on the host copy and by a device kernel. */
+int canvox_octree_hash(uint64_t* host_hash, uint64_t* device_hash);
+
+/*
+ * Time a grid of schedules (block size, blocks per SM, refill threshold,
+ * shared-memory prefix, frame levels) on these views and keep the fastest as
+ * the default options. Synchronous. Writes the chosen options to *best when
+ * best is not NULL.
+ */
+int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, canvox_render_opts* best);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* canvox_last_error(void);
+
+/* Free every device and pinned allocation of the library (safe to call twice). */
+void canvox_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CANVOX_H */

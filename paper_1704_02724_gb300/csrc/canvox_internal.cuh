@@ -1,0 +1,109 @@
+// Internal types shared by the CUDA translation units of libcanvox.so.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/canvox.h"
+
+namespace canvox {
+
+// Rays are handed out in tiles of 8 x 4 pixels (one warp); a view of W x H
+// pixels has ceil(W/8) x ceil(H/4) tiles, ray g of the launch is lane g % 32 of
+// tile g / 32.
+constexpr int kTileW = 8;
+constexpr int kTileH = 4;
+constexpr int kMaxDepth = 30;
+
+// Device view of the uploaded canvas.
+struct Tree {
+    const int32_t* nodes;  // n_rec x 8 child slots
+    const uint2* leaves;   // n_leaf x FP16 (R,G | B,sigma)
+    int64_t n_rec;
+    int64_t n_leaf;
+    int32_t depth;
+    int32_t pad;
+    double extent;
+    double half;  // extent / 2
+};
+
+// Per-view set-up, computed on the host in FP64 from canvox_camera.
+struct View {
+    double eye[3];
+    double f[3], u[3], r[3];  // orthonormal frame (Gram-Schmidt from forward)
+    double sx, sy;            // tan * aspect, tan
+    double two_over_w, two_over_h;
+    float bg[4];
+    int64_t out_offset;
+    int64_t ray_begin;  // first ray index of this view in the launch (multiple of 32)
+    int32_t width, height;
+    int32_t tiles_x;
+    int32_t pad;
+};
+
+// Counters, in the order of canvox_stats.
+enum Stat {
+    kStatRays = 0,
+    kStatSteps,
+    kStatSlotReads,
+    kStatLeafLoads,
+    kStatRecordLoads,
+    kStatFp64Boundaries,
+    kStatRebases,
+    kStatStepLimited,
+    kNumStats
+};
+
+// Device scratch: ray queue heads, counters, status word (zeroed before a launch).
+struct Scratch {
+    unsigned long long stats[kNumStats];
+    unsigned long long status;
+    unsigned long long queue[1];  // one head per launch (per view in per-view mode)
+};
+
+struct MixedParams {
+    Tree tree;
+    const View* views;
+    int32_t n_views;
+    int32_t refill;
+    int64_t total_rays;  // the queue hands out rays [0, total_rays) ...
+    int64_t ray_base;    // ... which are rays ray_base + g of the view table
+    float4* out;
+    int32_t* step_count;
+    unsigned long long* queue;
+    Scratch* scratch;
+    int64_t step_limit;
+    float t_min;
+    float err_budget;
+    int32_t frame_levels;
+    int32_t smem_records;
+};
+
+struct PlainParams {
+    Tree tree;
+    const View* view;  // one view per launch
+    float4* out;
+    int32_t* step_count;
+    Scratch* scratch;
+    int64_t step_limit;
+    float t_min;
+};
+
+// Launchers (trace_mixed.cu, trace_plain.cu, runtime.cu).
+cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s);
+cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out);
+cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
+cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
+
+// 64-bit element hash shared by the host and device hash of the pools.
+__host__ __device__ inline unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline unsigned long long elem_hash(unsigned long long tag, unsigned long long index,
+                                                        unsigned long long value) {
+    return mix64(tag ^ mix64(index * 0x9E3779B97F4A7C15ull + value));
+}
+
+}  // namespace canvox

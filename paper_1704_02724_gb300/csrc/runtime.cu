@@ -1,0 +1,639 @@
+// libcanvox.so runtime: the C ABI of include/canvox.h.
+//
+// Host side of the renderer: canvas validation and upload (Sec. 4.1: linear
+// index pools, eight children per allocation unit, copied to the GPU), the
+// host/device bit-identity hash, per-view FP64 set-up of the eye and pixel
+// grid (Sec. 6.1), launch of the traversal kernels, CUDA-graph replay,
+// counters and the schedule autotuner.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "canvox_internal.cuh"
+
+using namespace canvox;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky launch error if it is not a context error
+    return fail(e == cudaErrorMemoryAllocation ? CANVOX_ERR_OOM : CANVOX_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct GraphEntry {
+    bool valid = false;
+    int buf = 0;
+    const void* out = nullptr;
+    int32_t n_views = 0;
+    int64_t total_rays = 0;
+    unsigned long long layout = 0;  // hash of every view's size and offset
+    canvox_render_opts opts{};
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct Ctx {
+    int device = -1;
+    int sm_count = 0;
+    // canvas
+    int32_t* d_nodes = nullptr;
+    uint2* d_leaves = nullptr;
+    int64_t n_rec = 0, n_leaf = 0;
+    int32_t depth = 0;
+    double extent = 0.0;
+    unsigned long long host_hash = 0;
+    bool uploaded = false;
+    // views: device table and two pinned staging buffers, each guarded by an event
+    View* d_views = nullptr;
+    int views_cap = 0;
+    View* h_views[2] = {nullptr, nullptr};
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    int next_buf = 0;
+    // scratch: counters, status and one queue head per launch
+    Scratch* d_scratch = nullptr;
+    int scratch_queues = 0;
+    unsigned long long* d_hash = nullptr;
+    cudaEvent_t done = nullptr;  // recorded after every render
+    bool any_render = false;
+    int64_t last_h2d = 0, last_d2h = 0;
+    // host render target
+    float4* d_host_out = nullptr;
+    int64_t host_out_cap = 0;
+    // defaults (autotuned)
+    canvox_render_opts tuned{};
+    bool have_tuned = false;
+    GraphEntry graphs[4];
+    int graph_next = 0;
+};
+
+Ctx g;
+
+size_t scratch_bytes(int queues) { return sizeof(Scratch) + sizeof(unsigned long long) * (size_t)(queues > 1 ? queues - 1 : 0); }
+
+void builtin_defaults(canvox_render_opts* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->precision = CANVOX_PREC_MIXED;
+    o->per_view = 0;
+    o->use_graph = 0;
+    o->block_threads = 256;
+    o->blocks_per_sm = 0;
+    o->refill = 8;
+    o->smem_records = 0;
+    o->frame_levels = 12;
+    o->step_limit = 0;
+    o->t_min = -1.0f;
+    o->err_budget = 3.0e-6f;
+    o->step_count = nullptr;
+}
+
+int ensure_device() {
+    int dev;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (g.device >= 0 && g.device != dev)
+        return fail(CANVOX_ERR_INVALID_ARG, "canvas was uploaded on device %d, current device is %d", g.device, dev);
+    if (g.device < 0) {
+        g.device = dev;
+        CK(cudaDeviceGetAttribute(&g.sm_count, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+        CK(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming), "cudaEventCreate");
+        for (int b = 0; b < 2; ++b) CK(cudaEventCreateWithFlags(&g.staged[b], cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaMalloc(&g.d_hash, sizeof(unsigned long long)), "cudaMalloc(hash)");
+    }
+    return CANVOX_OK;
+}
+
+void drop_graphs() {
+    for (auto& e : g.graphs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        e = GraphEntry();
+    }
+}
+
+int ensure_views(int n) {
+    if (n <= g.views_cap) return CANVOX_OK;
+    int cap = 64;
+    while (cap < n) cap *= 2;
+    // wait for every user of the old buffers, then grow
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    drop_graphs();
+    if (g.d_views) cudaFree(g.d_views);
+    for (int b = 0; b < 2; ++b)
+        if (g.h_views[b]) cudaFreeHost(g.h_views[b]);
+    g.d_views = nullptr;
+    g.h_views[0] = g.h_views[1] = nullptr;
+    g.views_cap = 0;
+    CK(cudaMalloc(&g.d_views, sizeof(View) * (size_t)cap), "cudaMalloc(views)");
+    for (int b = 0; b < 2; ++b) CK(cudaMallocHost(&g.h_views[b], sizeof(View) * (size_t)cap), "cudaMallocHost(views)");
+    g.views_cap = cap;
+    return CANVOX_OK;
+}
+
+int ensure_scratch(int queues) {
+    if (queues <= g.scratch_queues) return CANVOX_OK;
+    int cap = 64;
+    while (cap < queues) cap *= 2;
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    drop_graphs();
+    if (g.d_scratch) cudaFree(g.d_scratch);
+    g.d_scratch = nullptr;
+    g.scratch_queues = 0;
+    CK(cudaMalloc(&g.d_scratch, scratch_bytes(cap)), "cudaMalloc(scratch)");
+    CK(cudaMemset(g.d_scratch, 0, scratch_bytes(cap)), "cudaMemset(scratch)");
+    g.scratch_queues = cap;
+    return CANVOX_OK;
+}
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Per-view set-up in FP64: Gram-Schmidt frame from forward, pixel scale factors, tiling.
+int setup_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays) {
+    int64_t ray = 0;
+    for (int v = 0; v < n; ++v) {
+        const canvox_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1 || !(c.tan_half_fov_y > 0.0) || !std::isfinite(c.tan_half_fov_y) ||
+            c.out_offset_px < 0 || !finite3(c.eye) || !finite3(c.right) || !finite3(c.up) || !finite3(c.forward))
+            return fail(CANVOX_ERR_INVALID_ARG, "camera %d: bad size, field of view, offset or non-finite vector", v);
+        for (int a = 0; a < 4; ++a)
+            if (!std::isfinite(c.background[a])) return fail(CANVOX_ERR_INVALID_ARG, "camera %d: non-finite background", v);
+        View& V = out[v];
+        std::memset(&V, 0, sizeof(V));
+        double n0 = std::sqrt(dot3(c.forward, c.forward));
+        if (!(n0 > 0.0)) return fail(CANVOX_ERR_INVALID_ARG, "camera %d: zero forward vector", v);
+        for (int a = 0; a < 3; ++a) V.f[a] = c.forward[a] / n0;
+        const double uf = dot3(c.up, V.f);
+        for (int a = 0; a < 3; ++a) V.u[a] = c.up[a] - uf * V.f[a];
+        double n1 = std::sqrt(dot3(V.u, V.u));
+        if (!(n1 > 0.0)) return fail(CANVOX_ERR_INVALID_ARG, "camera %d: up is parallel to forward", v);
+        for (int a = 0; a < 3; ++a) V.u[a] /= n1;
+        const double rf = dot3(c.right, V.f), ru = dot3(c.right, V.u);
+        for (int a = 0; a < 3; ++a) V.r[a] = c.right[a] - rf * V.f[a] - ru * V.u[a];
+        double n2 = std::sqrt(dot3(V.r, V.r));
+        if (!(n2 > 0.0)) return fail(CANVOX_ERR_INVALID_ARG, "camera %d: right is in the forward/up plane", v);
+        for (int a = 0; a < 3; ++a) V.r[a] /= n2;
+        for (int a = 0; a < 3; ++a) V.eye[a] = c.eye[a];
+        V.sy = c.tan_half_fov_y;
+        V.sx = c.tan_half_fov_y * ((double)c.width / (double)c.height);
+        V.two_over_w = 2.0 / (double)c.width;
+        V.two_over_h = 2.0 / (double)c.height;
+        for (int a = 0; a < 4; ++a) V.bg[a] = c.background[a];
+        V.out_offset = c.out_offset_px;
+        V.width = c.width;
+        V.height = c.height;
+        V.tiles_x = (c.width + kTileW - 1) / kTileW;
+        const int64_t tiles = (int64_t)V.tiles_x * ((c.height + kTileH - 1) / kTileH);
+        V.ray_begin = ray;
+        ray += tiles * 32;
+    }
+    *total_rays = ray;
+    return CANVOX_OK;
+}
+
+int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
+    if (in) *o = *in;
+    else canvox_default_opts(o);
+    if (o->precision < 0 || o->precision > 2) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
+    if (o->block_threads == 0) o->block_threads = 256;
+    if (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)
+        return fail(CANVOX_ERR_INVALID_ARG, "block_threads %d (multiple of 32, at most 256)", o->block_threads);
+    if (o->refill < 0 || o->refill > 31) return fail(CANVOX_ERR_INVALID_ARG, "refill %d (0..31)", o->refill);
+    if (o->frame_levels == 0) o->frame_levels = 12;
+    if (o->frame_levels < 1 || o->frame_levels > 22) return fail(CANVOX_ERR_INVALID_ARG, "frame_levels %d (1..22)", o->frame_levels);
+    if (o->blocks_per_sm < 0 || o->smem_records < 0 || o->step_limit < 0)
+        return fail(CANVOX_ERR_INVALID_ARG, "negative schedule option");
+    if (!(o->err_budget >= 0.0f) || !std::isfinite(o->err_budget)) return fail(CANVOX_ERR_INVALID_ARG, "err_budget");
+    if (!std::isfinite(o->t_min)) return fail(CANVOX_ERR_INVALID_ARG, "t_min");
+    if (o->t_min < 0.0f) o->t_min = 9.5367431640625e-07f;  // 2^-20
+    if (o->step_limit == 0) {
+        const int64_t lim = 3 * ((int64_t)1 << g.depth) + 8;
+        o->step_limit = lim > 0x7FFFFFFF ? 0x7FFFFFFF : lim;
+    }
+    if (o->blocks_per_sm == 0) {
+        int b = 0;
+        CK(mixed_max_blocks_per_sm(o->block_threads, 0, &b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        o->blocks_per_sm = b > 0 ? b : 1;
+    }
+    return CANVOX_OK;
+}
+
+Tree device_tree() {
+    Tree t;
+    t.nodes = g.d_nodes;
+    t.leaves = g.d_leaves;
+    t.n_rec = g.n_rec;
+    t.n_leaf = g.n_leaf;
+    t.depth = g.depth;
+    t.pad = 0;
+    t.extent = g.extent;
+    t.half = 0.5 * g.extent;
+    return t;
+}
+
+// The launch sequence of one render: stage views, clear scratch, trace.
+int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, float* out,
+            const canvox_render_opts& o, cudaStream_t s) {
+    const int queues = o.per_view ? n : 1;
+    CK(cudaMemcpyAsync(g.d_views, hv, sizeof(View) * (size_t)n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(views)");
+    CK(cudaMemsetAsync(g.d_scratch, 0, scratch_bytes(queues), s), "cudaMemsetAsync(scratch)");
+    const Tree t = device_tree();
+    if (o.precision == CANVOX_PREC_MIXED) {
+        MixedParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.tree = t;
+        p.out = reinterpret_cast<float4*>(out);
+        p.step_count = o.step_count;
+        p.scratch = g.d_scratch;
+        p.step_limit = o.step_limit;
+        p.t_min = o.t_min;
+        p.err_budget = o.err_budget;
+        p.frame_levels = o.frame_levels;
+        p.refill = o.refill;
+        p.smem_records = o.smem_records;
+        if (!o.per_view) {
+            p.views = g.d_views;
+            p.n_views = n;
+            p.total_rays = total_rays;
+            p.ray_base = 0;
+            p.queue = g.d_scratch->queue;
+            const int grid = g.sm_count * o.blocks_per_sm;
+            CK(launch_mixed(p, grid, o.block_threads, s), "mixed kernel launch");
+        } else {
+            for (int v = 0; v < n; ++v) {
+                p.views = g.d_views + v;
+                p.n_views = 1;
+                const int64_t rays = (v + 1 < n ? views_host[v + 1].ray_begin : total_rays) - views_host[v].ray_begin;
+                p.total_rays = rays;
+                p.ray_base = views_host[v].ray_begin;
+                p.queue = g.d_scratch->queue + v;
+                int64_t blocks = (rays + o.block_threads - 1) / o.block_threads;
+                int64_t cap = (int64_t)g.sm_count * o.blocks_per_sm;
+                const int grid = (int)(blocks < cap ? blocks : cap);
+                CK(launch_mixed(p, grid > 0 ? grid : 1, o.block_threads, s), "mixed kernel launch");
+            }
+        }
+    } else {
+        PlainParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.tree = t;
+        p.out = reinterpret_cast<float4*>(out);
+        p.step_count = o.step_count;
+        p.scratch = g.d_scratch;
+        p.step_limit = o.step_limit;
+        p.t_min = o.t_min;
+        for (int v = 0; v < n; ++v) {
+            p.view = g.d_views + v;
+            CK(launch_plain(p, o.precision, (long long)views_host[v].width * views_host[v].height, s), "plain kernel launch");
+        }
+    }
+    return CANVOX_OK;
+}
+
+bool same_opts(const canvox_render_opts& a, const canvox_render_opts& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+void canvox_default_opts(canvox_render_opts* o) {
+    if (!o) return;
+    if (g.have_tuned) *o = g.tuned;
+    else builtin_defaults(o);
+}
+
+const char* canvox_last_error(void) { return g_err.c_str(); }
+
+int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint16_t* leaf_rgba, int64_t n_leaves,
+                         int32_t depth, double extent) {
+    g_err.clear();
+    if (!node_pool || n_records < 1 || n_leaves < 0 || (n_leaves > 0 && !leaf_rgba))
+        return fail(CANVOX_ERR_INVALID_ARG, "null pool or bad count");
+    if (n_records > 0x7FFFFFFFll || n_leaves > 0x7FFFFFFFll)
+        return fail(CANVOX_ERR_INVALID_ARG, "pool larger than int32 indices");
+    if (depth < 1 || depth > kMaxDepth) return fail(CANVOX_ERR_INVALID_ARG, "depth %d not in 1..30", depth);
+    if (!(extent > 0.0) || !std::isfinite(extent)) return fail(CANVOX_ERR_INVALID_ARG, "extent must be finite and > 0");
+    {
+        int ex;
+        const double m = std::frexp(extent, &ex);  // m in [0.5, 1)
+        const double scaled = std::ldexp(m, 23);  // integer iff at most 23 significant bits
+        if (scaled != std::floor(scaled))
+            return fail(CANVOX_ERR_INVALID_ARG, "extent %.17g has more than 23 significant bits", extent);
+    }
+    // validation: breadth-first numbering of records and leaves, depth bound, finite FP16 values
+    std::vector<uint8_t> level((size_t)n_records, 0);
+    int64_t next_rec = 1, next_leaf = 0;
+    unsigned long long hh = 0;
+    for (int64_t r = 0; r < n_records; ++r) {
+        if (r >= next_rec) return fail(CANVOX_ERR_BAD_TREE, "record %lld is not referenced before it appears", (long long)r);
+        for (int k = 0; k < 8; ++k) {
+            const int32_t v = node_pool[8 * r + k];
+            hh += elem_hash(1ull, (unsigned long long)(8 * r + k), (unsigned long long)(uint32_t)v);
+            if (v > 0) {
+                if (v != next_rec)
+                    return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: child %d, expected %lld (breadth-first order)",
+                                (long long)r, k, v, (long long)next_rec);
+                if (v >= n_records) return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: child %d out of range", (long long)r, k, v);
+                if (level[r] + 1 > depth - 1)
+                    return fail(CANVOX_ERR_BAD_TREE, "record %d at level %d exceeds depth %d", v, level[r] + 1, depth);
+                level[v] = (uint8_t)(level[r] + 1);
+                ++next_rec;
+            } else if (v < 0) {
+                const int64_t li = -(int64_t)v - 1;
+                if (li != next_leaf)
+                    return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: leaf %lld, expected %lld (breadth-first order)",
+                                (long long)r, k, (long long)li, (long long)next_leaf);
+                if (li >= n_leaves) return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: leaf %lld out of range", (long long)r, k, (long long)li);
+                ++next_leaf;
+            }
+        }
+    }
+    if (next_rec != n_records) return fail(CANVOX_ERR_BAD_TREE, "%lld records unreachable", (long long)(n_records - next_rec));
+    if (next_leaf != n_leaves) return fail(CANVOX_ERR_BAD_TREE, "%lld leaves unreferenced", (long long)(n_leaves - next_leaf));
+    for (int64_t i = 0; i < n_leaves; ++i) {
+        const uint16_t* q = leaf_rgba + 4 * i;
+        for (int c = 0; c < 4; ++c)
+            if (((q[c] >> 10) & 31) == 31) return fail(CANVOX_ERR_BAD_TREE, "leaf %lld: non-finite FP16", (long long)i);
+        if ((q[3] & 0x8000u) && (q[3] & 0x7FFFu)) return fail(CANVOX_ERR_BAD_TREE, "leaf %lld: negative extinction", (long long)i);
+        unsigned long long val = (unsigned long long)q[0] | ((unsigned long long)q[1] << 16) |
+                                 ((unsigned long long)q[2] << 32) | ((unsigned long long)q[3] << 48);
+        hh += elem_hash(2ull, (unsigned long long)i, val);
+    }
+    int rc = ensure_device();
+    if (rc) return rc;
+    // replace the device copy
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    drop_graphs();
+    if (g.d_nodes) cudaFree(g.d_nodes);
+    if (g.d_leaves) cudaFree(g.d_leaves);
+    g.d_nodes = nullptr;
+    g.d_leaves = nullptr;
+    g.uploaded = false;
+    CK(cudaMalloc(&g.d_nodes, sizeof(int32_t) * 8 * (size_t)n_records), "cudaMalloc(nodes)");
+    CK(cudaMalloc(&g.d_leaves, sizeof(uint2) * (size_t)(n_leaves > 0 ? n_leaves : 1)), "cudaMalloc(leaves)");
+    CK(cudaMemcpy(g.d_nodes, node_pool, sizeof(int32_t) * 8 * (size_t)n_records, cudaMemcpyHostToDevice), "cudaMemcpy(nodes)");
+    if (n_leaves > 0)
+        CK(cudaMemcpy(g.d_leaves, leaf_rgba, sizeof(uint2) * (size_t)n_leaves, cudaMemcpyHostToDevice), "cudaMemcpy(leaves)");
+    g.n_rec = n_records;
+    g.n_leaf = n_leaves;
+    g.depth = depth;
+    g.extent = extent;
+    g.host_hash = hh;
+    // bit-identity of the device copy
+    CK(cudaMemset(g.d_hash, 0, sizeof(unsigned long long)), "cudaMemset(hash)");
+    CK(launch_hash(device_tree(), g.d_hash, 0), "hash kernel launch");
+    unsigned long long dh = 0;
+    CK(cudaMemcpy(&dh, g.d_hash, sizeof(dh), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
+    if (dh != hh) return fail(CANVOX_ERR_CUDA, "device copy hash %016llx differs from host %016llx", dh, hh);
+    g.uploaded = true;
+    return CANVOX_OK;
+}
+
+int canvox_octree_hash(uint64_t* host_hash, uint64_t* device_hash) {
+    g_err.clear();
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    if (host_hash) *host_hash = g.host_hash;
+    if (device_hash) {
+        if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+        CK(cudaMemset(g.d_hash, 0, sizeof(unsigned long long)), "cudaMemset(hash)");
+        CK(launch_hash(device_tree(), g.d_hash, 0), "hash kernel launch");
+        unsigned long long dh = 0;
+        CK(cudaMemcpy(&dh, g.d_hash, sizeof(dh), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
+        *device_hash = dh;
+    }
+    return CANVOX_OK;
+}
+
+int canvox_render_ex(const canvox_camera* cams, int32_t n_views, float* out_rgba_dev, void* stream,
+                     const canvox_render_opts* opts) {
+    g_err.clear();
+    if (n_views < 0 || (n_views > 0 && (!cams || !out_rgba_dev))) return fail(CANVOX_ERR_INVALID_ARG, "null cameras/output or n_views < 0");
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    int rc = ensure_device();
+    if (rc) return rc;
+    canvox_render_opts o;
+    rc = resolve_opts(opts, &o);
+    if (rc) return rc;
+    if (n_views == 0) return CANVOX_OK;
+    std::vector<View> views((size_t)n_views);
+    int64_t total_rays = 0;
+    rc = setup_views(cams, n_views, views.data(), &total_rays);
+    if (rc) return rc;
+    if ((rc = ensure_views(n_views)) || (rc = ensure_scratch(o.per_view ? n_views : 1))) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int b = g.next_buf;
+    g.next_buf ^= 1;
+    // the staging buffer b may still feed an earlier render's copy
+    CK(cudaEventSynchronize(g.staged[b]), "cudaEventSynchronize(staging)");
+    std::memcpy(g.h_views[b], views.data(), sizeof(View) * (size_t)n_views);
+    // renders share the library's scratch: order this one after the previous one
+    if (g.any_render) CK(cudaStreamWaitEvent(s, g.done, 0), "cudaStreamWaitEvent");
+    if (o.use_graph) {
+        unsigned long long layout = 0;
+        for (int v = 0; v < n_views; ++v)
+            layout = mix64(layout ^ mix64(((unsigned long long)cams[v].width << 32) ^ (unsigned long long)cams[v].height) ^
+                           (unsigned long long)cams[v].out_offset_px);
+        GraphEntry* hit = nullptr;
+        for (auto& e : g.graphs)
+            if (e.valid && e.buf == b && e.out == out_rgba_dev && e.n_views == n_views && e.total_rays == total_rays &&
+                e.layout == layout && same_opts(e.opts, o))
+                hit = &e;
+        if (!hit) {
+            GraphEntry& e = g.graphs[g.graph_next];
+            g.graph_next = (g.graph_next + 1) % 4;
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+            e = GraphEntry();
+            cudaStream_t cs;
+            CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+            cudaGraph_t graph;
+            cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (ce != cudaSuccess) {
+                cudaStreamDestroy(cs);
+                return cuda_fail(ce, "cudaStreamBeginCapture");
+            }
+            int erc = enqueue(g.h_views[b], views.data(), n_views, total_rays, out_rgba_dev, o, cs);
+            ce = cudaStreamEndCapture(cs, &graph);
+            cudaStreamDestroy(cs);
+            if (erc) return erc;
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&e.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+            e.valid = true;
+            e.buf = b;
+            e.out = out_rgba_dev;
+            e.n_views = n_views;
+            e.total_rays = total_rays;
+            e.layout = layout;
+            e.opts = o;
+            hit = &e;
+        }
+        CK(cudaGraphLaunch(hit->exec, s), "cudaGraphLaunch");
+    } else {
+        rc = enqueue(g.h_views[b], views.data(), n_views, total_rays, out_rgba_dev, o, s);
+        if (rc) return rc;
+    }
+    CK(cudaEventRecord(g.staged[b], s), "cudaEventRecord");
+    CK(cudaEventRecord(g.done, s), "cudaEventRecord");
+    g.any_render = true;
+    g.last_h2d = (int64_t)sizeof(View) * n_views;
+    g.last_d2h = 0;
+    return CANVOX_OK;
+}
+
+int canvox_render(const canvox_camera* cams, int32_t n_views, float* out_rgba_dev, void* stream) {
+    return canvox_render_ex(cams, n_views, out_rgba_dev, stream, nullptr);
+}
+
+int canvox_get_stats(canvox_stats* s) {
+    g_err.clear();
+    if (!s) return fail(CANVOX_ERR_INVALID_ARG, "null stats");
+    std::memset(s, 0, sizeof(*s));
+    if (!g.any_render) return CANVOX_OK;
+    CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    Scratch h;
+    CK(cudaMemcpy(&h, g.d_scratch, sizeof(Scratch), cudaMemcpyDeviceToHost), "cudaMemcpy(stats)");
+    s->rays = (int64_t)h.stats[kStatRays];
+    s->steps = (int64_t)h.stats[kStatSteps];
+    s->slot_reads = (int64_t)h.stats[kStatSlotReads];
+    s->leaf_loads = (int64_t)h.stats[kStatLeafLoads];
+    s->record_loads = (int64_t)h.stats[kStatRecordLoads];
+    s->fp64_boundaries = (int64_t)h.stats[kStatFp64Boundaries];
+    s->rebases = (int64_t)h.stats[kStatRebases];
+    s->step_limited = (int64_t)h.stats[kStatStepLimited];
+    s->h2d_bytes = g.last_h2d;
+    s->d2h_bytes = g.last_d2h;
+    if (h.status) return fail(CANVOX_ERR_STEP_LIMIT, "%lld rays stopped at the step limit", (long long)s->step_limited);
+    return CANVOX_OK;
+}
+
+int canvox_render_host(const canvox_camera* cams, int32_t n_views, float* out_rgba_host, void* stream,
+                       const canvox_render_opts* opts) {
+    g_err.clear();
+    if (n_views < 0 || (n_views > 0 && (!cams || !out_rgba_host))) return fail(CANVOX_ERR_INVALID_ARG, "null cameras/output");
+    if (n_views == 0) return CANVOX_OK;
+    int64_t npx = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (cams[v].width < 1 || cams[v].height < 1 || cams[v].out_offset_px < 0)
+            return fail(CANVOX_ERR_INVALID_ARG, "camera %d: bad size or offset", v);
+        const int64_t e = cams[v].out_offset_px + (int64_t)cams[v].width * cams[v].height;
+        if (e > npx) npx = e;
+    }
+    if (npx > g.host_out_cap) {
+        if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+        drop_graphs();
+        if (g.d_host_out) cudaFree(g.d_host_out);
+        g.d_host_out = nullptr;
+        g.host_out_cap = 0;
+        CK(cudaMalloc(&g.d_host_out, sizeof(float4) * (size_t)npx), "cudaMalloc(host render target)");
+        g.host_out_cap = npx;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = canvox_render_ex(cams, n_views, reinterpret_cast<float*>(g.d_host_out), stream, opts);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out_rgba_host, g.d_host_out, sizeof(float4) * (size_t)npx, cudaMemcpyDeviceToHost, s),
+       "cudaMemcpyAsync(image)");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    g.last_d2h = (int64_t)sizeof(float4) * npx;
+    unsigned long long status = 0;
+    CK(cudaMemcpy(&status, &g.d_scratch->status, sizeof(status), cudaMemcpyDeviceToHost), "cudaMemcpy(status)");
+    if (status) return fail(CANVOX_ERR_STEP_LIMIT, "rays stopped at the step limit");
+    return CANVOX_OK;
+}
+
+int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, canvox_render_opts* best) {
+    g_err.clear();
+    if (n_views < 1 || !cams) return fail(CANVOX_ERR_INVALID_ARG, "autotune needs at least one camera");
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    int64_t npx = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int64_t e = cams[v].out_offset_px + (int64_t)cams[v].width * cams[v].height;
+        if (e > npx) npx = e;
+    }
+    float4* out = nullptr;
+    CK(cudaMalloc(&out, sizeof(float4) * (size_t)(npx > 0 ? npx : 1)), "cudaMalloc(autotune target)");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    canvox_render_opts base;
+    builtin_defaults(&base);
+    canvox_render_opts win = base;
+    float best_ms = 1e30f;
+    const int blocks[] = {128, 256};
+    const int refills[] = {0, 4, 8, 16, 24};
+    const int frames[] = {8, 12, 16};
+    int rc = CANVOX_OK;
+    for (int bt : blocks)
+        for (int rf : refills)
+            for (int fl : frames) {
+                canvox_render_opts o = base;
+                o.block_threads = bt;
+                o.refill = rf;
+                o.frame_levels = fl;
+                o.blocks_per_sm = 0;
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 3 && rc == CANVOX_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    rc = canvox_render_ex(cams, n_views, reinterpret_cast<float*>(out), stream, &o);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < ms_min) ms_min = ms;
+                }
+                if (rc) break;
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    win = o;
+                    win.blocks_per_sm = 0;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(out);
+    if (rc) return rc;
+    g.tuned = win;
+    g.have_tuned = true;
+    if (best) *best = win;
+    return CANVOX_OK;
+}
+
+void canvox_release(void) {
+    if (g.device < 0) return;
+    cudaDeviceSynchronize();
+    drop_graphs();
+    if (g.d_nodes) cudaFree(g.d_nodes);
+    if (g.d_leaves) cudaFree(g.d_leaves);
+    if (g.d_views) cudaFree(g.d_views);
+    for (int b = 0; b < 2; ++b) {
+        if (g.h_views[b]) cudaFreeHost(g.h_views[b]);
+        if (g.staged[b]) cudaEventDestroy(g.staged[b]);
+    }
+    if (g.d_scratch) cudaFree(g.d_scratch);
+    if (g.d_hash) cudaFree(g.d_hash);
+    if (g.d_host_out) cudaFree(g.d_host_out);
+    if (g.done) cudaEventDestroy(g.done);
+    g = Ctx();
+}
+
+}  // extern "C"

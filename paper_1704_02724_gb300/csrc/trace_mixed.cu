@@ -1,0 +1,501 @@
+// Mixed-precision persistent ray caster for deep sparse octrees (sm_103a).
+//
+// One lane traces one ray (Sec. 6 of the paper): from the FP64 eye (Sec. 6.1)
+// leaf by leaf through the octree, compositing front to back, until the
+// transmittance drops below t_min or the ray leaves the canvas (Sec. 6.2).
+//
+// Cells are addressed by exact integer coordinates (level L, c in [0, 2^L)^3).
+// Crossing a face moves c by one on the exit axis; the lowest common ancestor
+// of the old and new cell is L - bitlength(c_old ^ c_new), and the new leaf is
+// found by re-descending from that ancestor's record, kept on a per-lane stack
+// of records by level. The integer bits fix the path down to the old cell's
+// level; only deeper levels need the ray's position.
+//
+// Precision (Sec. 6.1-6.3): the ray is evaluated in FP32 inside a local frame,
+// a cell of level f <= L (at most K levels above the leaf), in frame units:
+//     t'(P') = P' inv_d + nod_f,   t' = (t - t_f) / S_f,
+// where P' is a cell plane in frame units (exact dyadic), t_f the FP64 ray
+// parameter where the frame was entered and S_f its size. This is the paper's
+// cell-local frame (origin at a cell, unit size), generalised from one cell to
+// a subtree, and re-anchored in FP64 whenever the ray leaves the frame, so the
+// drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames.
+// Every FP32 crossing time is within 2^-22 |inv_d_a| frame units of the exact
+// value. Decisions whose two sides are closer than that bound (exit axis near
+// an edge, child choice near a mid-plane) are retaken in FP64. A boundary
+// between leaves of different value moves the pixel by at most
+// 2 T max(sigma) |dt|; each ray carries a budget for these bounds, and a
+// boundary whose bound would exceed it is recomputed in FP64. The FP64 form of
+// a crossing is t = P inv_d + nod (P an exact FP64 plane).
+//
+// Compositing (emission-absorption reading of Sec. 6.2): per segment of length
+// l in a leaf (sigma, rgb): a = 1 - exp(-sigma l), C += T a rgb, tau += sigma l,
+// T = exp(-tau), with compensated (Kahan) FP32 sums for C and tau.
+#include <cuda_fp16.h>
+
+#include "canvox_internal.cuh"
+
+namespace canvox {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr float kEps22 = 2.384185791015625e-07f;  // 2^-22: FP32 crossing-time bound per |inv_d|
+constexpr float kEps21 = 4.76837158203125e-07f;   // 2^-21 = 2 * 2^-22: factor 2 of the colour bound
+
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ float hsig(uint2 v) { return __half2float(__ushort_as_half((unsigned short)(v.y >> 16))); }
+__device__ __forceinline__ float hlo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
+__device__ __forceinline__ float hhi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+
+__device__ __forceinline__ int32_t load_slot(const Tree& T, int32_t rec, int k) {
+    return __ldg(T.nodes + (int64_t)rec * 8 + k);
+}
+__device__ __forceinline__ uint2 load_leaf(const Tree& T, int32_t slot) { return __ldg(T.leaves + (-(int64_t)slot - 1)); }
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+struct Ray {
+    double inv64[3], nod64[3];  // t(P) = P inv + nod; axis with d = 0: inv = 0, nod = o
+    double tf;                  // FP64 ray parameter at the frame origin
+    double invS;                // 1 / frame size
+    float inv32[3], nodf[3];    // frame-local: t'(P') = P' inv + nodf; d = 0: nodf = position
+    float sf, sf_eps;           // frame size, frame size * 2^-21
+    float cur_hi, cur_lo;       // frame-local parameter of the current leaf's entry (double-float)
+    float C0, C1, C2, k0, k1, k2;
+    float tau, ktau, T;
+    float err;
+    uint32_t c[3];
+    int32_t L, f;
+    uint32_t dpos, zmask;
+    uint2 val;
+    int32_t steps;
+    int32_t view;
+    int64_t pix;
+    // counters, summed over every ray the lane traces
+    uint32_t n_rays, n_steps, n_reads, n_leaf, n_rec, n_f64, n_rebase;
+};
+
+__device__ __forceinline__ bool is_zero(const Ray& r, int a) { return (r.zmask >> a) & 1u; }
+
+// Ray on the high side of the global plane x_a = M just after parameter t (FP64).
+__device__ __forceinline__ uint32_t high64(const Ray& r, int a, double M, double t) {
+    if (is_zero(r, a)) return r.nod64[a] >= M;
+    const double tm = fma(M, r.inv64[a], r.nod64[a]);
+    return r.inv64[a] > 0.0 ? (tm <= t) : (tm > t);
+}
+
+// Exact FP64 crossing time of the face (c + s) of a level-L cell on axis a.
+__device__ __forceinline__ double face_t64(const Ray& r, const Tree& T, int a, uint32_t cs, int L) {
+    const double P = fma((double)cs, T.extent * pow2d(-L), -T.half);
+    return fma(P, r.inv64[a], r.nod64[a]);
+}
+
+__device__ __forceinline__ void split_local(const Ray& r, double t, float& hi, float& lo) {
+    const double tl = (t - r.tf) * r.invS;
+    hi = (float)tl;
+    lo = (float)(tl - (double)hi);
+}
+
+// Enter the frame at level r.f that holds the current cell; t = FP64 parameter of the entry.
+__device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_extent, double t) {
+    r.tf = t;
+    const int sh = r.L - r.f;
+    const double Sf = T.extent * pow2d(-r.f);
+    r.invS = pow2d(r.f) * inv_extent;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double Fmin = fma((double)(r.c[a] >> sh), Sf, -T.half);
+        if (is_zero(r, a)) r.nodf[a] = (float)((r.nod64[a] - Fmin) * r.invS);
+        else r.nodf[a] = (float)((fma(Fmin, r.inv64[a], r.nod64[a]) - t) * r.invS);
+    }
+    r.sf = (float)Sf;
+    r.sf_eps = r.sf * kEps21;
+    r.cur_hi = 0.0f;
+    r.cur_lo = 0.0f;
+    r.n_rebase += 1;
+}
+
+__device__ __forceinline__ void composite(Ray& r, float teh, float tel) {
+    const float ell = fmaxf(0.0f, (teh - r.cur_hi) + (tel - r.cur_lo)) * r.sf;
+    if (r.val.y >> 16) {
+        const float s = hsig(r.val);
+        const float x = s * ell;
+        const float a = -expm1f(-x);
+        const float w = r.T * a;
+        kahan_add(r.C0, r.k0, w * hlo(r.val.x));
+        kahan_add(r.C1, r.k1, w * hhi(r.val.x));
+        kahan_add(r.C2, r.k2, w * hlo(r.val.y));
+        kahan_add(r.tau, r.ktau, x);
+        r.T = expf(-r.tau);
+    }
+}
+
+__device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
+    const View& V = P.views[r.view];
+    float4 o;
+    o.x = r.C0 + r.T * V.bg[0];
+    o.y = r.C1 + r.T * V.bg[1];
+    o.z = r.C2 + r.T * V.bg[2];
+    o.w = 1.0f - r.T;
+    P.out[r.pix] = o;
+    if (P.step_count) P.step_count[r.pix] = r.steps;
+    r.n_rays += 1;
+    r.n_steps += (uint32_t)r.steps;
+}
+
+// Start ray g of the launch. Returns true if it has a leaf to step from.
+__device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsigned long long g, int32_t* stk) {
+    const Tree& T = P.tree;
+    g += (unsigned long long)P.ray_base;
+    int lo = 0, hi = P.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)P.views[mid].ray_begin <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const View& V = P.views[lo];
+    const long long local = (long long)g - V.ray_begin;
+    const long long tile = local >> 5;
+    const int lane = (int)(local & 31);
+    const int i = (int)(tile % V.tiles_x) * kTileW + (lane & (kTileW - 1));
+    const int j = (int)(tile / V.tiles_x) * kTileH + (lane / kTileW);
+    if (i >= V.width || j >= V.height) return false;  // padding lane of a ragged tile
+    r.view = lo;
+    r.pix = V.out_offset + (int64_t)j * V.width + i;
+    r.C0 = r.C1 = r.C2 = r.k0 = r.k1 = r.k2 = 0.0f;
+    r.tau = r.ktau = 0.0f;
+    r.T = 1.0f;
+    r.err = 0.0f;
+    r.steps = 0;
+    // pixel-centre ray in FP64 (Sec. 6.1)
+    const double u = fma(2.0 * i + 1.0, V.two_over_w * 0.5, -1.0) * V.sx;
+    const double v = fma(-(2.0 * j + 1.0), V.two_over_h * 0.5, 1.0) * V.sy;
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = V.f[a] + u * V.r[a] + v * V.u[a];
+    const double nrm = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    r.dpos = 0;
+    r.zmask = 0;
+    double t0 = 0.0, t1 = __longlong_as_double(0x7FF0000000000000ll);
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double da = d[a] * nrm;
+        const double o = V.eye[a];
+        if (da != 0.0) {
+            r.inv64[a] = 1.0 / da;
+            r.nod64[a] = -o * r.inv64[a];
+            r.inv32[a] = (float)r.inv64[a];
+            if (da > 0.0) r.dpos |= 1u << a;
+            const double ta = fma(-T.half, r.inv64[a], r.nod64[a]);
+            const double tb = fma(T.half, r.inv64[a], r.nod64[a]);
+            t0 = fmax(t0, da > 0.0 ? ta : tb);
+            t1 = fmin(t1, da > 0.0 ? tb : ta);
+        } else {
+            r.inv64[a] = 0.0;
+            r.nod64[a] = o;
+            r.inv32[a] = 0.0f;
+            r.zmask |= 1u << a;
+            if (!(o >= -T.half && o < T.half)) miss = true;
+        }
+    }
+    if (miss || !(t0 < t1)) {
+        finish(r, P);
+        return false;
+    }
+    // locate the leaf that holds r(t0+) from the root, in FP64
+    uint32_t cc[3] = {0u, 0u, 0u};
+    int lev = 0;
+    int32_t rec = 0;
+    int32_t slot;
+    stk[0] = 0;
+    for (;;) {
+        const double w = T.extent * pow2d(-(lev + 1));
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double M = fma((double)(2u * cc[a] + 1u), w, -T.half);
+            const uint32_t b = high64(r, a, M, t0);
+            cc[a] = 2u * cc[a] + b;
+            k |= (int)b << a;
+        }
+        slot = load_slot(T, rec, k);
+        r.n_rec += 1;
+        if (slot > 0) {
+            ++lev;
+            stk[lev] = slot;
+            rec = slot;
+        } else {
+            break;
+        }
+    }
+    r.L = lev + 1;
+    r.n_reads += r.L;
+    r.c[0] = cc[0];
+    r.c[1] = cc[1];
+    r.c[2] = cc[2];
+    if (slot < 0) {
+        r.val = load_leaf(T, slot);
+        r.n_leaf += 1;
+    } else {
+        r.val = make_uint2(0u, 0u);
+    }
+    r.steps = 1;
+    r.f = max(0, r.L - P.frame_levels);
+    set_frame(r, T, inv_extent, t0);
+    return true;
+}
+
+// One leaf step. Returns false once the ray is finished (its pixel written).
+__device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_t* stk) {
+    const Tree& T = P.tree;
+    // 1. exit of the current leaf in the FP32 frame
+    const int kf = r.L - r.f;
+    const float sc = pow2f(-kf);
+    const uint32_t fmask = (1u << kf) - 1u;
+    float te[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (is_zero(r, a)) {
+            te[a] = __int_as_float(0x7F800000);
+        } else {
+            const uint32_t rel = (r.c[a] & fmask) + ((r.dpos >> a) & 1u);
+            te[a] = fmaf((float)rel * sc, r.inv32[a], r.nodf[a]);
+        }
+    }
+    int ax = 0;
+    if (te[1] < te[ax]) ax = 1;
+    if (te[2] < te[ax]) ax = 2;
+    const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+    const int a2 = te[b2] < te[b1] ? b2 : b1;
+    float teh = te[ax], tel = 0.0f;
+    bool have64 = false;
+    double te64 = 0.0;
+    if (te[a2] - te[ax] <= kEps22 * (fabsf(r.inv32[ax]) + fabsf(r.inv32[a2]))) {
+        // the exit face is ambiguous in FP32 (ray near an edge): decide in FP64
+        double best = __longlong_as_double(0x7FF0000000000000ll);
+        int bax = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (is_zero(r, a)) continue;
+            const double ta = face_t64(r, T, a, r.c[a] + ((r.dpos >> a) & 1u), r.L);
+            if (ta < best) { best = ta; bax = a; }
+        }
+        ax = bax;
+        te64 = best;
+        have64 = true;
+        split_local(r, te64, teh, tel);
+        r.n_f64 += 1;
+    }
+    // 2. neighbour across the exit face
+    const uint32_t up = (r.dpos >> ax) & 1u;
+    const uint32_t cold = r.c[ax];
+    const uint32_t cn = up ? cold + 1u : cold - 1u;
+    if ((cn >> r.L) != 0u) {
+        // leaving the canvas: last segment, bounded like a boundary to sigma = 0
+        if (!have64 && (r.val.y >> 16)) {
+            const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(r.inv32[ax]);
+            if (r.err + need > P.err_budget) {
+                te64 = face_t64(r, T, ax, cold + up, r.L);
+                have64 = true;
+                split_local(r, te64, teh, tel);
+                r.n_f64 += 1;
+            } else {
+                r.err += need;
+            }
+        }
+        composite(r, teh, tel);
+        finish(r, P);
+        return false;
+    }
+    const int lstar = r.L - (32 - __clz(cold ^ cn));
+    const bool fexit = lstar < r.f;
+    if (fexit && !have64) {
+        te64 = face_t64(r, T, ax, cold + up, r.L);
+        have64 = true;
+        split_local(r, te64, teh, tel);
+    }
+    // 3. re-descend from the common ancestor
+    uint32_t cc[3] = {r.c[0], r.c[1], r.c[2]};
+    cc[ax] = cn;
+    int Lc = r.L;
+    int lev = lstar;
+    int32_t rec = stk[lstar];
+    int32_t slot;
+    for (;;) {
+        int k;
+        if (lev < Lc) {
+            const int sh = Lc - 1 - lev;
+            k = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
+        } else {
+            // finer than the old cell: near side on the exit axis, ray position on the others
+            k = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                uint32_t bit;
+                if (a == ax) {
+                    bit = up ? 0u : 1u;
+                } else {
+                    bool decided = false;
+                    bit = 0u;
+                    if (!fexit && lev - r.f < 22) {
+                        const uint32_t rel = cc[a] & ((1u << (lev - r.f)) - 1u);
+                        const float Mp = (float)(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
+                        if (is_zero(r, a)) {
+                            // parallel to the plane: exact in FP64 unless the FP32 position is too close
+                            if (fabsf(r.nodf[a] - Mp) > kEps22) {
+                                bit = r.nodf[a] >= Mp;
+                                decided = true;
+                            }
+                        } else {
+                            const float tm = fmaf(Mp, r.inv32[a], r.nodf[a]);
+                            if (fabsf(tm - teh) > kEps22 * (fabsf(r.inv32[a]) + fabsf(r.inv32[ax]))) {
+                                bit = r.inv32[a] > 0.0f ? (tm <= teh) : (tm > teh);
+                                decided = true;
+                            }
+                        }
+                    }
+                    if (!decided) {
+                        if (!have64) {
+                            te64 = face_t64(r, T, ax, cold + up, r.L);
+                            have64 = true;
+                            split_local(r, te64, teh, tel);
+                            r.n_f64 += 1;
+                        }
+                        const double M = fma((double)(2u * cc[a] + 1u), T.extent * pow2d(-(lev + 1)), -T.half);
+                        bit = high64(r, a, M, te64);
+                    }
+                }
+                cc[a] = 2u * cc[a] + bit;
+                k |= (int)bit << a;
+            }
+            ++Lc;
+        }
+        slot = load_slot(T, rec, k);
+        r.n_rec += 1;
+        if (slot > 0) {
+            ++lev;
+            stk[lev] = slot;
+            rec = slot;
+        } else {
+            break;
+        }
+    }
+    const int Ln = lev + 1;
+    r.n_reads += (uint32_t)(Ln - lstar);
+    uint2 nval = make_uint2(0u, 0u);
+    if (slot < 0) {
+        nval = load_leaf(T, slot);
+        r.n_leaf += 1;
+    }
+    const bool rebase = fexit || (Ln - r.f > P.frame_levels);
+    // 4. precision of this boundary
+    if (!have64) {
+        if (rebase) {
+            te64 = face_t64(r, T, ax, cold + up, r.L);
+            have64 = true;
+            split_local(r, te64, teh, tel);
+        } else if (nval.x != r.val.x || nval.y != r.val.y) {
+            const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(r.inv32[ax]);
+            if (r.err + need > P.err_budget) {
+                te64 = face_t64(r, T, ax, cold + up, r.L);
+                have64 = true;
+                split_local(r, te64, teh, tel);
+                r.n_f64 += 1;
+            } else {
+                r.err += need;
+            }
+        }
+    }
+    // 5. composite the current leaf, then terminate or advance
+    composite(r, teh, tel);
+    if (r.T < P.t_min) {
+        finish(r, P);
+        return false;
+    }
+    if (r.steps >= P.step_limit) {
+        atomicOr(&P.scratch->status, 1ull);
+        atomicAdd(&P.scratch->stats[kStatStepLimited], 1ull);
+        finish(r, P);
+        return false;
+    }
+    const int sh = Lc - Ln;
+    r.c[0] = cc[0] >> sh;
+    r.c[1] = cc[1] >> sh;
+    r.c[2] = cc[2] >> sh;
+    r.L = Ln;
+    r.val = nval;
+    r.steps += 1;
+    if (rebase) {
+        r.f = max(0, Ln - P.frame_levels);
+        set_frame(r, T, inv_extent, te64);
+    } else {
+        r.cur_hi = teh;
+        r.cur_lo = tel;
+    }
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) mixed_kernel(MixedParams P) {
+    int32_t stk[kMaxDepth + 1];
+    Ray r;
+    r.n_rays = r.n_steps = r.n_reads = r.n_leaf = r.n_rec = r.n_f64 = r.n_rebase = 0;
+    const double inv_extent = 1.0 / P.tree.extent;
+    const unsigned lane = threadIdx.x & 31u;
+    bool alive = false;
+    bool drained = false;
+    for (;;) {
+        unsigned busy = __ballot_sync(kFull, alive);
+        if (!drained && __popc(busy) <= P.refill) {
+            const unsigned idle = ~busy;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(P.queue, (unsigned long long)__popc(idle));
+            base = __shfl_sync(kFull, base, 0);
+            if (base + __popc(idle) >= (unsigned long long)P.total_rays) drained = true;
+            if (!alive) {
+                const unsigned long long g = base + __popc(idle & ((1u << lane) - 1u));
+                if (g < (unsigned long long)P.total_rays) alive = ray_init(r, P, inv_extent, g, stk);
+            }
+            busy = __ballot_sync(kFull, alive);
+            if (!drained && __popc(busy) <= P.refill) continue;
+        }
+        if (busy == 0u) {
+            if (drained) break;
+            continue;
+        }
+        do {
+            if (alive) alive = ray_step(r, P, inv_extent, stk);
+            busy = __ballot_sync(kFull, alive);
+        } while (busy != 0u && (drained || __popc(busy) > P.refill));
+    }
+    const unsigned long long v[7] = {r.n_rays, r.n_steps, r.n_reads, r.n_leaf, r.n_rec, r.n_f64, r.n_rebase};
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const unsigned long long s = warp_sum(v[i]);
+        if (lane == 0 && s) atomicAdd(&P.scratch->stats[i], s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s) {
+    mixed_kernel<<<grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel, block, smem_bytes);
+}
+
+}  // namespace canvox

@@ -1,0 +1,38 @@
+"""Helpers for the GPU parity tests: canvas cache, renders through the C ABI."""
+import functools
+
+import numpy as np
+
+import paper_1704_02724_gb300 as cx
+import synth
+
+TOL = 1e-5   # max abs error per channel of the GPU image against the FP64 oracle
+
+_uploaded = {"key": None}
+
+
+@functools.lru_cache(maxsize=4)
+def config_canvas(cid, n_fine=None):
+    return synth.build_config(cid, n_fine=n_fine)
+
+
+def upload(canvas, key=None):
+    key = key if key is not None else id(canvas)
+    if _uploaded["key"] != key:
+        cx.upload_octree(canvas.nodes, canvas.leaves, canvas.depth, canvas.extent)
+        _uploaded["key"] = key
+
+
+def render(canvas, cams, key=None, fill=np.nan, **opts):
+    import torch
+    upload(canvas, key)
+    n = synth.total_pixels(cams)
+    out = torch.full((max(n, 1), 4), fill, dtype=torch.float32, device="cuda")
+    cx.render(cams, out, **opts)
+    torch.cuda.synchronize()
+    stats = cx.get_stats(check=False)
+    return out.cpu().numpy().astype(np.float64)[:n], stats
+
+
+def max_err(a, b):
+    return float(np.max(np.abs(a - b))) if a.size else 0.0

@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on a GPU.
+
+The bar is a max abs error of 1e-5 per channel (tests/gpu_util.TOL) for the
+mixed-precision and plain FP64 kernels, element by element on the same seeded
+inputs. Full images at sizes the oracle finishes in seconds; at the full
+benchmark size (c2, 2 x 2160^2 at depth 24) a seeded sample of pixels plus
+whole 64x64 tiles. The canvas-coordinate FP32 kernel is expected to fail the
+bar at depth >= 24 (Sec. 6.3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_02724_gb300 as cx
+from paper_1704_02724_gb300 import canvox
+import synth
+from synth import random_tree as rt
+from gpu_util import TOL, config_canvas, max_err, render, upload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_02724_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available()
+
+
+def test_upload_hash_bit_identity():
+    cv = config_canvas(0)
+    upload(cv, "c0")
+    h, d = cx.octree_hash()
+    assert h == d != 0
+
+
+def test_c0_full_image_mixed_and_fp64():
+    cv = config_canvas(0)
+    cams = synth.config_cameras(0)
+    ref, ic, _ = oracle.render(cv, cams, counters=True)
+    steps = torch.zeros(synth.total_pixels(cams), dtype=torch.int32, device="cuda")
+    img, st = render(cv, cams, key="c0", step_count=steps)
+    assert max_err(img, ref) <= TOL
+    # the leaf sequence is the oracle's: per-pixel leaf counts and aggregate reads
+    sc = steps.cpu().numpy()
+    assert np.mean(sc == ic[:, 0]) > 0.999
+    assert abs(st["steps"] - ic[:, 0].sum()) <= 1e-4 * ic[:, 0].sum()
+    assert abs(st["slot_reads"] - ic[:, 1].sum()) <= 1e-4 * ic[:, 1].sum()
+    assert abs(st["leaf_loads"] - ic[:, 2].sum()) <= 1e-4 * ic[:, 2].sum()
+    assert st["rays"] == 256 * 256
+    img64, st64 = render(cv, cams, key="c0", precision=cx.PREC_FP64)
+    assert max_err(img64, ref) <= 1e-6
+
+
+def _edge_cameras(extent):
+    E = extent
+    cams = []
+    off = 0
+
+    def add(eye, tgt, w, h, tan=0.6, up=(0, 1, 0), bg=(0.1, 0.2, 0.3, 1)):
+        nonlocal off
+        cams.append(synth.look_at_camera(np.array(eye) * E, np.array(tgt) * E, up, tan, w, h, off, bg))
+        off += w * h + 3   # gaps between views stay unwritten
+    add([1.7, 0.4, -1.1], [0.02, -0.03, 0.01], 37, 23)           # ragged tiles
+    add([0.1, 0.05, -0.2], [0.3, 0.1, 0.4], 16, 12, tan=1.0)       # eye inside the canvas
+    add([0.0, 0.0, 2.0], [0.0, 0.0, 0.0], 9, 9, tan=0.3)           # axis-aligned: zero direction components
+    add([0.25, 0.25, 1.5], [0.25, 0.25, 0.0], 5, 5, tan=0.2)       # on cell planes, axis-aligned
+    add([2.0, 2.0, 2.0], [0.0, 0.0, 0.0], 1, 1)                    # single pixel through a corner
+    add([3.0, 5.0, 0.0], [3.0, 6.0, 0.0], 8, 4)                    # looks away: all background
+    return synth.cameras_array(cams)
+
+
+@pytest.mark.parametrize("seed,depth,extent", [(1, 5, 1.0), (2, 6, 3.0), (3, 7, 1000.0), (4, 4, 40000.0)])
+def test_random_trees_edge_cameras(seed, depth, extent):
+    cv = rt.random_tree(depth, seed=500 + seed, p_refine=0.5, extent=extent)
+    cams = _edge_cameras(extent)
+    ref = oracle.render(cv, cams)
+    written = ~np.isnan(ref[:, 0])
+    for prec, tol in ((cx.PREC_MIXED, TOL), (cx.PREC_FP64, 1e-6)):
+        img, st = render(cv, cams, key=("rt", seed), precision=prec)
+        assert np.all(np.isnan(img[~written]))            # nothing outside the views is touched
+        assert max_err(img[written], ref[written]) <= tol, prec
+
+
+def test_t_min_zero_runs_to_canvas_exit():
+    cv = rt.random_tree(6, seed=77, p_refine=0.55, sigma_range=(0.5, 30.0))
+    cams = _edge_cameras(1.0)
+    ref = oracle.render(cv, cams, t_min=0.0)
+    w = ~np.isnan(ref[:, 0])
+    img, _ = render(cv, cams, key="t0", t_min=0.0)
+    assert max_err(img[w], ref[w]) <= TOL
+
+
+def _embedded_scene(level):
+    """A depth-4 random scene as one cell at `level` of a 40 km canvas (cell side 40000 * 2^-level)."""
+    small = rt.random_nested(4, seed=91, p_refine=0.6, sigma_range=(0.5, 20.0))
+    E = 40000.0
+    cell = (2 ** (level - 1) + 12345, 2 ** (level - 1) - 777, 2 ** (level - 2) + 5)
+    s = E * 2.0 ** -level
+    # extinction per metre so that the scene has the same optical depth per cell side
+    def scale(t):
+        if isinstance(t, list):
+            return [scale(c) for c in t]
+        if t is None:
+            return None
+        return (t[0], t[1], t[2], t[3] / s)
+    big = rt.from_nested(rt.embed(scale(small), 4, level, cell), level + 4, E)
+    lo = np.array([-0.5 * E + c * s for c in cell])
+    return big, lo, s
+
+
+@pytest.mark.parametrize("level", [20, 23, 26])
+def test_deep_embedding_mixed_passes_fp32_fails(level):
+    cv, lo, s = _embedded_scene(level)
+    centre = lo + 0.5 * s
+    cams = synth.cameras_array([
+        synth.look_at_camera(centre + np.array([1.3, 0.7, -1.9]) * s, centre, [0, 1, 0], 0.5, 48, 40, 0),
+        synth.look_at_camera(centre + np.array([0.1, -0.2, 0.15]) * s, centre + np.array([0.4, 0.3, -0.2]) * s,
+                             [0, 1, 0], 1.0, 32, 32, 48 * 40),
+    ])
+    ref = oracle.render(cv, cams)
+    img, _ = render(cv, cams, key=("deep", level))
+    assert max_err(img, ref) <= TOL
+    if level >= 23:
+        img32, _ = render(cv, cams, key=("deep", level), precision=cx.PREC_FP32)
+        assert max_err(img32, ref) > 1e-3   # canvas-coordinate FP32 drifts at this depth
+
+
+def test_c1_reduced_full_image():
+    cv = config_canvas(1)
+    cams = synth.config_cameras(1, res_scale=0.125)
+    ref = oracle.render(cv, cams)
+    img, st = render(cv, cams, key="c1")
+    assert max_err(img, ref) <= TOL
+
+
+def _sample_pixels(cams, n_random, n_tiles, seed):
+    rng = np.random.default_rng(seed)
+    total = synth.total_pixels(cams)
+    idx = set(rng.choice(total, size=min(n_random, total), replace=False).tolist())
+    for c in cams:
+        W, H, off = int(c["width"]), int(c["height"]), int(c["out_offset_px"])
+        for _ in range(n_tiles):
+            x0, y0 = rng.integers(0, max(1, W - 64)), rng.integers(0, max(1, H - 64))
+            for j in range(y0, min(H, y0 + 64)):
+                idx.update(range(off + j * W + x0, off + j * W + min(W, x0 + 64)))
+    return np.array(sorted(idx), dtype=np.int64)
+
+
+@pytest.mark.parametrize("cid,n_random", [(1, 20000), (2, 20000)])
+def test_full_size_sampled(cid, n_random):
+    """Full-size images in the benchmark's launch configuration; oracle on sampled pixels."""
+    cv = config_canvas(cid)
+    cams = synth.config_cameras(cid)
+    img, st = render(cv, cams, key=f"c{cid}")
+    assert st["status"] == 0
+    px = _sample_pixels(cams, n_random, 2, seed=cid)
+    ref = oracle.render(cv, cams, px_idx=px)
+    err = np.abs(img[px] - ref)
+    assert float(err.max()) <= TOL, (float(err.max()), int(np.sum(err.max(1) > TOL)))
+    assert np.all(np.isfinite(img))
+
+
+def test_schedules_agree_bitwise():
+    cv = config_canvas(0)
+    cams = _edge_cameras(1.0)
+    base, _ = render(cv, cams, key="c0")
+    for kw in (dict(per_view=1), dict(use_graph=1), dict(use_graph=1), dict(refill=0, block_threads=128),
+               dict(refill=31, blocks_per_sm=1)):
+        img, _ = render(cv, cams, key="c0", **kw)
+        np.testing.assert_array_equal(img, base, err_msg=str(kw))
+
+
+def test_render_host_matches_device():
+    cv = config_canvas(0)
+    cams = synth.config_cameras(0)
+    dev, _ = render(cv, cams, key="c0")
+    host = np.zeros((synth.total_pixels(cams), 4), np.float32)
+    cx.render_host(cams, host)
+    np.testing.assert_array_equal(host.astype(np.float64), dev)
+
+
+def test_step_limit_reports_status():
+    cv = config_canvas(0)
+    cams = synth.config_cameras(0)
+    img, st = render(cv, cams, key="c0", step_limit=3)
+    assert st["status"] == canvox.ERR_STEP_LIMIT and st["step_limited"] > 0
+    assert np.all(np.isfinite(img))
+    host = np.zeros((synth.total_pixels(cams), 4), np.float32)
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.render_host(cams, host, step_limit=3)
+    assert e.value.code == canvox.ERR_STEP_LIMIT
+    img2, st2 = render(cv, cams, key="c0")   # the next render starts clean
+    assert st2["status"] == 0
+
+
+def test_empty_canvas_zero_views_and_bad_cameras():
+    cv = rt.from_nested([None] * 8, 1, 40000.0)
+    cams = _edge_cameras(40000.0)
+    img, st = render(cv, cams, key="empty")
+    ref = oracle.render(cv, cams)
+    w = ~np.isnan(ref[:, 0])
+    assert np.array_equal(img[w].astype(np.float32), ref[w].astype(np.float32))
+    out = torch.zeros((4, 4), device="cuda")
+    cx.render(cams[:0], out)          # no views: no-op
+    bad = cams.copy()
+    bad[0]["width"] = 0
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.render(bad, out)
+    assert e.value.code == canvox.ERR_INVALID_ARG
+    bad = cams.copy()
+    bad[1]["tan_half_fov_y"] = math.nan
+    with pytest.raises(cx.CanvoxError):
+        cx.render(bad, out)
+
+
+def test_bad_upload_keeps_previous_canvas():
+    cv = config_canvas(0)
+    upload(cv, "c0")
+    bad = cv.nodes.copy()
+    bad[0, 0] = 7
+    with pytest.raises(cx.CanvoxError):
+        cx.upload_octree(bad, cv.leaves, cv.depth, cv.extent)
+    cams = synth.config_cameras(0, res_scale=0.25)
+    img, _ = render(cv, cams, key="c0")
+    assert max_err(img, oracle.render(cv, cams)) <= TOL
