@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 baseline, e2e and CPU baseline")
     ap.add_argument("--opts", type=str, default="", help="render options as JSON")
+    ap.add_argument("--res-scale", type=float, default=1.0, help="shrink every image side (profiling cases)")
+    ap.add_argument("--n-fine", type=int, default=0, help="fine stamps of configs 2-4 (profiling cases; 0 = config)")
     return ap.parse_args()
 
 
@@ -214,8 +216,8 @@ def main():
 
     cid = args.config
     opts = json.loads(args.opts) if args.opts else {}
-    canvas = synth.build_config(cid)
-    cams = synth.config_cameras(cid)
+    canvas = synth.build_config(cid, n_fine=args.n_fine or None)
+    cams = synth.config_cameras(cid, res_scale=args.res_scale)
     n_px = synth.total_pixels(cams)
     cx.upload_octree(canvas.nodes, canvas.leaves, canvas.depth, canvas.extent)
     h_hash, d_hash = cx.octree_hash()
@@ -260,7 +262,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
-            "config": {"workload": workload_name(cid) + f" ({len(cams)} views, {n_px} rays, depth {canvas.depth},"
+            "config": {"workload": workload_name(cid) + (f" [reduced: res x{args.res_scale}, n_fine {args.n_fine}]"
+                                                         if args.res_scale != 1.0 or args.n_fine else "")
+                       + f" ({len(cams)} views, {n_px} rays, depth {canvas.depth},"
                        f" {canvas.n_records} records, {canvas.n_leaves} leaves)",
                        "rays_per_step": rays * world, "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": f"replicas x{world}", "opts": cx.default_opts() | opts},

@@ -54,7 +54,14 @@ extern "C" {
  *       (C + T bg.rgb, 1 - T) with T the transmittance left at the end.
  * Pixel (i, j) shoots the ray through its centre:
  *   d = normalize(f + u r + v up), u = (2(i+1/2)/W - 1) tan * W/H,
- *   v = (1 - 2(j+1/2)/H) tan.
+ *   v = (1 - 2(j+1/2)/H) tan,
+ * with f, up, r the orthonormalised frame. Every operation is IEEE FP64,
+ * rounded separately (no fused multiply-add), in this order:
+ *   x = (2i+1)/W - 1, y = 1 - (2j+1)/H, u = (x tan) (W/H), v = y tan,
+ *   d = (f + u r) + v up, d /= sqrt((d0 d0 + d1 d1) + d2 d2).
+ * A ray that lies exactly in a cell plane (a zero component of d, as in the
+ * centre row or column of an axis-aligned view) then stays exactly in it, and
+ * the side it runs on is the high side of that plane.
  */
 typedef struct canvox_camera {
     double eye[3];

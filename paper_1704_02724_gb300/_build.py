@@ -9,7 +9,7 @@ LIB = os.path.join(HERE, "libcanvox.so")
 SOURCES = ["runtime.cu", "trace_mixed.cu", "trace_plain.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 
 
 def _inputs():

@@ -27,11 +27,13 @@ struct Tree {
     double half;  // extent / 2
 };
 
-// Per-view set-up, computed on the host in FP64 from canvox_camera.
+// Per-view set-up, computed on the host in FP64 from canvox_camera (host code is
+// compiled without contraction, so the frame is the one the camera model defines).
 struct View {
     double eye[3];
     double f[3], u[3], r[3];  // orthonormal frame (Gram-Schmidt from forward)
     double sx, sy;            // tan * aspect, tan
+    double aspect;            // width / height
     double two_over_w, two_over_h;
     float bg[4];
     int64_t out_offset;
@@ -106,4 +108,25 @@ __host__ __device__ inline unsigned long long elem_hash(unsigned long long tag, 
     return mix64(tag ^ mix64(index * 0x9E3779B97F4A7C15ull + value));
 }
 
+}  // namespace canvox
+
+namespace canvox {
+// Unit direction of the ray through the centre of pixel (i, j) of view V, in
+// IEEE FP64 with every operation rounded separately in the order the camera
+// model of include/canvox.h fixes:
+//   x = (2i+1)/W - 1,  y = 1 - (2j+1)/H,  u = (x tan) aspect,  v = y tan,
+//   d = (f + u r) + v up,  d /= sqrt((d0 d0 + d1 d1) + d2 d2).
+// A ray that lies exactly in a cell plane (d_a == 0) must come out exactly so,
+// since the side of the plane it runs on is decided by this value.
+__device__ __forceinline__ void pixel_ray(const View& V, int i, int j, double d[3]) {
+    const double x = __dadd_rn(__ddiv_rn(2.0 * i + 1.0, (double)V.width), -1.0);
+    const double y = __dsub_rn(1.0, __ddiv_rn(2.0 * j + 1.0, (double)V.height));
+    const double u = __dmul_rn(__dmul_rn(x, V.sy), V.aspect);
+    const double v = __dmul_rn(y, V.sy);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = __dadd_rn(__dadd_rn(V.f[a], __dmul_rn(u, V.r[a])), __dmul_rn(v, V.u[a]));
+    const double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = __ddiv_rn(d[a], n);
+}
 }  // namespace canvox

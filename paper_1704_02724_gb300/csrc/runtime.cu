@@ -193,7 +193,8 @@ int setup_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays
         for (int a = 0; a < 3; ++a) V.r[a] /= n2;
         for (int a = 0; a < 3; ++a) V.eye[a] = c.eye[a];
         V.sy = c.tan_half_fov_y;
-        V.sx = c.tan_half_fov_y * ((double)c.width / (double)c.height);
+        V.aspect = (double)c.width / (double)c.height;
+        V.sx = c.tan_half_fov_y * V.aspect;
         V.two_over_w = 2.0 / (double)c.width;
         V.two_over_h = 2.0 / (double)c.height;
         for (int a = 0; a < 4; ++a) V.bg[a] = c.background[a];

@@ -120,8 +120,12 @@ __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_exte
     r.n_rebase += 1;
 }
 
+// Composite the current leaf over [cursor, te]. The length is not clamped at
+// zero: an FP32 boundary can land slightly before the cursor (within its error
+// bound), and only the signed lengths of consecutive segments telescope, so a
+// boundary between two leaves of equal value then costs nothing.
 __device__ __forceinline__ void composite(Ray& r, float teh, float tel) {
-    const float ell = fmaxf(0.0f, (teh - r.cur_hi) + (tel - r.cur_lo)) * r.sf;
+    const float ell = ((teh - r.cur_hi) + (tel - r.cur_lo)) * r.sf;
     if (r.val.y >> 16) {
         const float s = hsig(r.val);
         const float x = s * ell;
@@ -173,19 +177,15 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     r.err = 0.0f;
     r.steps = 0;
     // pixel-centre ray in FP64 (Sec. 6.1)
-    const double u = fma(2.0 * i + 1.0, V.two_over_w * 0.5, -1.0) * V.sx;
-    const double v = fma(-(2.0 * j + 1.0), V.two_over_h * 0.5, 1.0) * V.sy;
     double d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = V.f[a] + u * V.r[a] + v * V.u[a];
-    const double nrm = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    pixel_ray(V, i, j, d);
     r.dpos = 0;
     r.zmask = 0;
     double t0 = 0.0, t1 = __longlong_as_double(0x7FF0000000000000ll);
     bool miss = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double da = d[a] * nrm;
+        const double da = d[a];
         const double o = V.eye[a];
         if (da != 0.0) {
             r.inv64[a] = 1.0 / da;

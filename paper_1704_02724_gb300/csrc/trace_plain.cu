@@ -49,19 +49,19 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
     const int i = (int)(idx % V.width), j = (int)(idx / V.width);
     const Tree& T = P.tree;
     const R E = (R)T.extent, half = (R)T.half;
-    // pixel-centre ray, entirely in R
-    const R u = N::fma_((R)(2 * i + 1), (R)(V.two_over_w * 0.5), (R)-1) * (R)V.sx;
-    const R v = N::fma_(-(R)(2 * j + 1), (R)(V.two_over_h * 0.5), (R)1) * (R)V.sy;
+    // pixel-centre ray: the camera model's FP64 ray, rounded to R
     R o[3], d[3], inv[3], nod[3];
-    for (int a = 0; a < 3; ++a) {
-        o[a] = (R)V.eye[a];
-        d[a] = (R)V.f[a] + u * (R)V.r[a] + v * (R)V.u[a];
+    {
+        double dd[3];
+        pixel_ray(V, i, j, dd);
+        for (int a = 0; a < 3; ++a) {
+            o[a] = (R)V.eye[a];
+            d[a] = (R)dd[a];
+        }
     }
-    const R nrm = N::rsqrt_(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     R t0 = 0, t1 = N::inf();
     bool miss = false;
     for (int a = 0; a < 3; ++a) {
-        d[a] *= nrm;
         if (d[a] != (R)0) {
             inv[a] = (R)1 / d[a];
             nod[a] = -o[a] * inv[a];
