@@ -100,7 +100,7 @@ void builtin_defaults(canvox_render_opts* o) {
     o->blocks_per_sm = 0;
     o->refill = 8;
     o->smem_records = 0;
-    o->frame_levels = 12;
+    o->frame_levels = 20;
     o->step_limit = 0;
     o->t_min = -1.0f;
     o->err_budget = 3.0e-6f;
@@ -218,7 +218,7 @@ int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)
         return fail(CANVOX_ERR_INVALID_ARG, "block_threads %d (multiple of 32, at most 256)", o->block_threads);
     if (o->refill < 0 || o->refill > 31) return fail(CANVOX_ERR_INVALID_ARG, "refill %d (0..31)", o->refill);
-    if (o->frame_levels == 0) o->frame_levels = 12;
+    if (o->frame_levels == 0) o->frame_levels = 20;
     if (o->frame_levels < 1 || o->frame_levels > 22) return fail(CANVOX_ERR_INVALID_ARG, "frame_levels %d (1..22)", o->frame_levels);
     if (o->blocks_per_sm < 0 || o->smem_records < 0 || o->step_limit < 0)
         return fail(CANVOX_ERR_INVALID_ARG, "negative schedule option");

@@ -11,25 +11,26 @@
 // of records by level. The integer bits fix the path down to the old cell's
 // level; only deeper levels need the ray's position.
 //
-// Precision (Sec. 6.1-6.3): the ray is evaluated in FP32 inside a local frame,
-// a cell of level f <= L (at most K levels above the leaf), in frame units:
+// Precision (Sec. 6.1-6.3). The ray is evaluated inside a local frame, a cell
+// of level f <= L at most K levels above the leaf, in frame units:
 //     t'(P') = P' inv_d + nod_f,   t' = (t - t_f) / S_f,
-// where P' is a cell plane in frame units (exact dyadic), t_f the FP64 ray
-// parameter where the frame was entered and S_f its size. This is the paper's
-// cell-local frame (origin at a cell, unit size), generalised from one cell to
-// a subtree, and re-anchored in FP64 whenever the ray leaves the frame, so the
-// drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames.
-// Every FP32 crossing time is within 2^-22 |inv_d_a| frame units of the exact
-// value. Decisions whose two sides are closer than that bound (exit axis near
-// an edge, child choice near a mid-plane) are retaken in FP64. A boundary
-// between leaves of different value moves the pixel by at most
+// where P' is a cell plane in frame units (an exact dyadic FP32 value), t_f the
+// FP64 ray parameter where the frame was entered and S_f its size. This is the
+// paper's cell-local frame (origin at a cell, unit size) widened from one cell
+// to a subtree. The frame is re-anchored in FP64 whenever the ray leaves it, so
+// the drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames.
+// Inside a frame every crossing time is a double-float: an unevaluated sum
+// hi + lo of two FP32 words formed with error-free transformations (Dekker's
+// product by fma, Knuth's two-sum), good to about 2^-44 |inv_d| frame units.
+// Decisions closer than that bound (exit axis near an edge, child choice near
+// a mid-plane) are retaken in FP64 from exact planes: t = P inv_d + nod.
+// A boundary between leaves of different value moves the pixel by at most
 // 2 T max(sigma) |dt|; each ray carries a budget for these bounds, and a
-// boundary whose bound would exceed it is recomputed in FP64. The FP64 form of
-// a crossing is t = P inv_d + nod (P an exact FP64 plane).
+// boundary whose bound would exceed it is recomputed in FP64.
 //
-// Compositing (emission-absorption reading of Sec. 6.2): per segment of length
-// l in a leaf (sigma, rgb): a = 1 - exp(-sigma l), C += T a rgb, tau += sigma l,
-// T = exp(-tau), with compensated (Kahan) FP32 sums for C and tau.
+// Compositing (emission-absorption reading of Sec. 6.2): per segment of signed
+// length l in a leaf (sigma, rgb): a = 1 - exp(-sigma l), C += T a rgb,
+// tau += sigma l, T = exp(-tau), with compensated (Kahan) FP32 sums for C, tau.
 #include <cuda_fp16.h>
 
 #include "canvox_internal.cuh"
@@ -38,14 +39,16 @@ namespace canvox {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr float kEps22 = 2.384185791015625e-07f;  // 2^-22: FP32 crossing-time bound per |inv_d|
-constexpr float kEps21 = 4.76837158203125e-07f;   // 2^-21 = 2 * 2^-22: factor 2 of the colour bound
+constexpr float kEpsDF = 5.684341886080802e-14f;   // 2^-44: double-float crossing-time bound per |inv_d|
+constexpr float kEpsDF2 = 1.1368683772161603e-13f; // 2^-43 = 2 * 2^-44: factor 2 of the colour bound
+constexpr int kMaxFrameBits = 22;                   // a frame spans at most 22 levels (exact FP32 planes)
 
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 __device__ __forceinline__ float hsig(uint2 v) { return __half2float(__ushort_as_half((unsigned short)(v.y >> 16))); }
 __device__ __forceinline__ float hlo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
 __device__ __forceinline__ float hhi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+__device__ __forceinline__ float finf() { return __int_as_float(0x7F800000); }
 
 __device__ __forceinline__ int32_t load_slot(const Tree& T, int32_t rec, int k) {
     return __ldg(T.nodes + (int64_t)rec * 8 + k);
@@ -59,13 +62,32 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// t'(P) = P (ih + il) + (nh + nl) as hi + lo. P is exact; the product error
+// comes from one fma and the sum error from Knuth's two-sum, both exact.
+__device__ __forceinline__ void df_cross(float P, float ih, float il, float nh, float nl, float& hi, float& lo) {
+    const float p = __fmul_rn(P, ih);
+    const float pe = __fmaf_rn(P, ih, -p);
+    const float s = __fadd_rn(p, nh);
+    const float v = __fsub_rn(s, p);
+    const float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(nh, v));
+    const float t = __fadd_rn(__fadd_rn(pe, se), __fmaf_rn(P, il, nl));
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// (ah + al) - (bh + bl), rounded to FP32.
+__device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl) {
+    return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
+}
+
 struct Ray {
     double inv64[3], nod64[3];  // t(P) = P inv + nod; axis with d = 0: inv = 0, nod = o
     double tf;                  // FP64 ray parameter at the frame origin
     double invS;                // 1 / frame size
-    float inv32[3], nodf[3];    // frame-local: t'(P') = P' inv + nodf; d = 0: nodf = position
-    float sf, sf_eps;           // frame size, frame size * 2^-21
-    float cur_hi, cur_lo;       // frame-local parameter of the current leaf's entry (double-float)
+    float ih[3], il[3];         // inv_d as two FP32 words (0 for d = 0)
+    float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
+    float sf, sf_eps;           // frame size, frame size * 2^-43
+    float cur_hi, cur_lo;       // frame-local parameter of the current leaf's entry
     float C0, C1, C2, k0, k1, k2;
     float tau, ktau, T;
     float err;
@@ -89,7 +111,7 @@ __device__ __forceinline__ uint32_t high64(const Ray& r, int a, double M, double
     return r.inv64[a] > 0.0 ? (tm <= t) : (tm > t);
 }
 
-// Exact FP64 crossing time of the face (c + s) of a level-L cell on axis a.
+// FP64 crossing time of the face (c + s) of a level-L cell on axis a (exact plane).
 __device__ __forceinline__ double face_t64(const Ray& r, const Tree& T, int a, uint32_t cs, int L) {
     const double P = fma((double)cs, T.extent * pow2d(-L), -T.half);
     return fma(P, r.inv64[a], r.nod64[a]);
@@ -101,7 +123,7 @@ __device__ __forceinline__ void split_local(const Ray& r, double t, float& hi, f
     lo = (float)(tl - (double)hi);
 }
 
-// Enter the frame at level r.f that holds the current cell; t = FP64 parameter of the entry.
+// Enter the frame at level r.f that holds the cell (r.L, r.c); t = FP64 parameter of the entry.
 __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_extent, double t) {
     r.tf = t;
     const int sh = r.L - r.f;
@@ -110,18 +132,19 @@ __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_exte
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double Fmin = fma((double)(r.c[a] >> sh), Sf, -T.half);
-        if (is_zero(r, a)) r.nodf[a] = (float)((r.nod64[a] - Fmin) * r.invS);
-        else r.nodf[a] = (float)((fma(Fmin, r.inv64[a], r.nod64[a]) - t) * r.invS);
+        const double n = is_zero(r, a) ? (r.nod64[a] - Fmin) * r.invS : (fma(Fmin, r.inv64[a], r.nod64[a]) - t) * r.invS;
+        r.nh[a] = (float)n;
+        r.nl[a] = (float)(n - (double)r.nh[a]);
     }
     r.sf = (float)Sf;
-    r.sf_eps = r.sf * kEps21;
+    r.sf_eps = r.sf * kEpsDF2;
     r.cur_hi = 0.0f;
     r.cur_lo = 0.0f;
     r.n_rebase += 1;
 }
 
 // Composite the current leaf over [cursor, te]. The length is not clamped at
-// zero: an FP32 boundary can land slightly before the cursor (within its error
+// zero: a boundary can land slightly before the cursor (within its error
 // bound), and only the signed lengths of consecutive segments telescope, so a
 // boundary between two leaves of equal value then costs nothing.
 __device__ __forceinline__ void composite(Ray& r, float teh, float tel) {
@@ -150,6 +173,30 @@ __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
     if (P.step_count) P.step_count[r.pix] = r.steps;
     r.n_rays += 1;
     r.n_steps += (uint32_t)r.steps;
+}
+
+// Child bit on axis a of the cell at level `lev` with coordinate cc, for the ray
+// just after the frame-local time (th, tl). Double-float with an ambiguity
+// margin (margin_t: the bound of (th, tl) itself), else FP64 at need64().
+template <typename Need64>
+__device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a, uint32_t cc, int lev, float th,
+                                              float tl, float margin_t, Need64 need64) {
+    if (lev - r.f < kMaxFrameBits) {
+        const uint32_t rel = cc & ((1u << (lev - r.f)) - 1u);
+        const float Mp = (float)(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
+        if (is_zero(r, a)) {
+            const float dm = __fadd_rn(__fsub_rn(r.nh[a], Mp), r.nl[a]);
+            if (fabsf(dm) > kEpsDF) return dm >= 0.0f;
+        } else {
+            float mh, ml;
+            df_cross(Mp, r.ih[a], r.il[a], r.nh[a], r.nl[a], mh, ml);
+            const float dm = df_diff(mh, ml, th, tl);
+            if (fabsf(dm) > kEpsDF * fabsf(r.ih[a]) + margin_t) return r.ih[a] > 0.0f ? (dm <= 0.0f) : (dm > 0.0f);
+        }
+    }
+    const double t64 = need64();
+    const double M = fma((double)(2u * cc + 1u), T.extent * pow2d(-(lev + 1)), -T.half);
+    return high64(r, a, M, t64);
 }
 
 // Start ray g of the launch. Returns true if it has a leaf to step from.
@@ -190,7 +237,8 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         if (da != 0.0) {
             r.inv64[a] = 1.0 / da;
             r.nod64[a] = -o * r.inv64[a];
-            r.inv32[a] = (float)r.inv64[a];
+            r.ih[a] = (float)r.inv64[a];
+            r.il[a] = (float)(r.inv64[a] - (double)r.ih[a]);
             if (da > 0.0) r.dpos |= 1u << a;
             const double ta = fma(-T.half, r.inv64[a], r.nod64[a]);
             const double tb = fma(T.half, r.inv64[a], r.nod64[a]);
@@ -199,7 +247,8 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         } else {
             r.inv64[a] = 0.0;
             r.nod64[a] = o;
-            r.inv32[a] = 0.0f;
+            r.ih[a] = 0.0f;
+            r.il[a] = 0.0f;
             r.zmask |= 1u << a;
             if (!(o >= -T.half && o < T.half)) miss = true;
         }
@@ -208,20 +257,28 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         finish(r, P);
         return false;
     }
-    // locate the leaf that holds r(t0+) from the root, in FP64
-    uint32_t cc[3] = {0u, 0u, 0u};
+    // locate the leaf that holds r(t0+) from the root, in double-float frames (frame time 0)
+    r.c[0] = r.c[1] = r.c[2] = 0u;
+    r.L = 0;
+    r.f = 0;
+    set_frame(r, T, inv_extent, t0);
     int lev = 0;
     int32_t rec = 0;
     int32_t slot;
     stk[0] = 0;
+    auto need64 = [&]() { return t0; };
     for (;;) {
-        const double w = T.extent * pow2d(-(lev + 1));
+        if (lev - r.f >= kMaxFrameBits) {
+            // planes of the next level need more than 22 bits in this frame: re-anchor at this cell
+            r.L = lev;
+            r.f = lev;
+            set_frame(r, T, inv_extent, t0);
+        }
         int k = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double M = fma((double)(2u * cc[a] + 1u), w, -T.half);
-            const uint32_t b = high64(r, a, M, t0);
-            cc[a] = 2u * cc[a] + b;
+            const uint32_t b = child_bit(r, T, a, r.c[a], lev, 0.0f, 0.0f, 0.0f, need64);
+            r.c[a] = 2u * r.c[a] + b;
             k |= (int)b << a;
         }
         slot = load_slot(T, rec, k);
@@ -236,9 +293,6 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     }
     r.L = lev + 1;
     r.n_reads += r.L;
-    r.c[0] = cc[0];
-    r.c[1] = cc[1];
-    r.c[2] = cc[2];
     if (slot < 0) {
         r.val = load_leaf(T, slot);
         r.n_leaf += 1;
@@ -246,38 +300,41 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         r.val = make_uint2(0u, 0u);
     }
     r.steps = 1;
-    r.f = max(0, r.L - P.frame_levels);
-    set_frame(r, T, inv_extent, t0);
+    if (r.L - r.f > P.frame_levels) {
+        r.f = r.L - P.frame_levels;
+        set_frame(r, T, inv_extent, t0);
+    }
     return true;
 }
 
 // One leaf step. Returns false once the ray is finished (its pixel written).
 __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_t* stk) {
     const Tree& T = P.tree;
-    // 1. exit of the current leaf in the FP32 frame
+    // 1. exit of the current leaf: double-float crossing times in the frame
     const int kf = r.L - r.f;
     const float sc = pow2f(-kf);
     const uint32_t fmask = (1u << kf) - 1u;
-    float te[3];
+    float th[3], tl[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (is_zero(r, a)) {
-            te[a] = __int_as_float(0x7F800000);
+            th[a] = finf();
+            tl[a] = 0.0f;
         } else {
             const uint32_t rel = (r.c[a] & fmask) + ((r.dpos >> a) & 1u);
-            te[a] = fmaf((float)rel * sc, r.inv32[a], r.nodf[a]);
+            df_cross((float)rel * sc, r.ih[a], r.il[a], r.nh[a], r.nl[a], th[a], tl[a]);
         }
     }
     int ax = 0;
-    if (te[1] < te[ax]) ax = 1;
-    if (te[2] < te[ax]) ax = 2;
+    if (th[1] < th[ax] || (th[1] == th[ax] && tl[1] < tl[ax])) ax = 1;
+    if (th[2] < th[ax] || (th[2] == th[ax] && tl[2] < tl[ax])) ax = 2;
     const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
-    const int a2 = te[b2] < te[b1] ? b2 : b1;
-    float teh = te[ax], tel = 0.0f;
+    const int a2 = (th[b2] < th[b1] || (th[b2] == th[b1] && tl[b2] < tl[b1])) ? b2 : b1;
+    float teh = th[ax], tel = tl[ax];
     bool have64 = false;
     double te64 = 0.0;
-    if (te[a2] - te[ax] <= kEps22 * (fabsf(r.inv32[ax]) + fabsf(r.inv32[a2]))) {
-        // the exit face is ambiguous in FP32 (ray near an edge): decide in FP64
+    if (df_diff(th[a2], tl[a2], th[ax], tl[ax]) <= kEpsDF * (fabsf(r.ih[ax]) + fabsf(r.ih[a2]))) {
+        // the exit face is ambiguous (ray within the bound of an edge): decide in FP64
         double best = __longlong_as_double(0x7FF0000000000000ll);
         int bax = 0;
 #pragma unroll
@@ -296,18 +353,22 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     const uint32_t up = (r.dpos >> ax) & 1u;
     const uint32_t cold = r.c[ax];
     const uint32_t cn = up ? cold + 1u : cold - 1u;
+    const int Lold = r.L;
+    auto need64 = [&]() {
+        if (!have64) {
+            te64 = face_t64(r, T, ax, cold + up, Lold);
+            have64 = true;
+            split_local(r, te64, teh, tel);
+            r.n_f64 += 1;
+        }
+        return te64;
+    };
     if ((cn >> r.L) != 0u) {
         // leaving the canvas: last segment, bounded like a boundary to sigma = 0
         if (!have64 && (r.val.y >> 16)) {
-            const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(r.inv32[ax]);
-            if (r.err + need > P.err_budget) {
-                te64 = face_t64(r, T, ax, cold + up, r.L);
-                have64 = true;
-                split_local(r, te64, teh, tel);
-                r.n_f64 += 1;
-            } else {
-                r.err += need;
-            }
+            const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(r.ih[ax]);
+            if (r.err + need > P.err_budget) need64();
+            else r.err += need;
         }
         composite(r, teh, tel);
         finish(r, P);
@@ -315,11 +376,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     }
     const int lstar = r.L - (32 - __clz(cold ^ cn));
     const bool fexit = lstar < r.f;
-    if (fexit && !have64) {
-        te64 = face_t64(r, T, ax, cold + up, r.L);
-        have64 = true;
-        split_local(r, te64, teh, tel);
-    }
+    if (fexit) need64();
     // 3. re-descend from the common ancestor
     uint32_t cc[3] = {r.c[0], r.c[1], r.c[2]};
     cc[ax] = cn;
@@ -327,6 +384,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     int lev = lstar;
     int32_t rec = stk[lstar];
     int32_t slot;
+    const float margin_ax = kEpsDF * fabsf(r.ih[ax]);
     for (;;) {
         int k;
         if (lev < Lc) {
@@ -340,36 +398,11 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
                 uint32_t bit;
                 if (a == ax) {
                     bit = up ? 0u : 1u;
+                } else if (fexit) {
+                    const double M = fma((double)(2u * cc[a] + 1u), T.extent * pow2d(-(lev + 1)), -T.half);
+                    bit = high64(r, a, M, te64);
                 } else {
-                    bool decided = false;
-                    bit = 0u;
-                    if (!fexit && lev - r.f < 22) {
-                        const uint32_t rel = cc[a] & ((1u << (lev - r.f)) - 1u);
-                        const float Mp = (float)(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
-                        if (is_zero(r, a)) {
-                            // parallel to the plane: exact in FP64 unless the FP32 position is too close
-                            if (fabsf(r.nodf[a] - Mp) > kEps22) {
-                                bit = r.nodf[a] >= Mp;
-                                decided = true;
-                            }
-                        } else {
-                            const float tm = fmaf(Mp, r.inv32[a], r.nodf[a]);
-                            if (fabsf(tm - teh) > kEps22 * (fabsf(r.inv32[a]) + fabsf(r.inv32[ax]))) {
-                                bit = r.inv32[a] > 0.0f ? (tm <= teh) : (tm > teh);
-                                decided = true;
-                            }
-                        }
-                    }
-                    if (!decided) {
-                        if (!have64) {
-                            te64 = face_t64(r, T, ax, cold + up, r.L);
-                            have64 = true;
-                            split_local(r, te64, teh, tel);
-                            r.n_f64 += 1;
-                        }
-                        const double M = fma((double)(2u * cc[a] + 1u), T.extent * pow2d(-(lev + 1)), -T.half);
-                        bit = high64(r, a, M, te64);
-                    }
+                    bit = child_bit(r, T, a, cc[a], lev, teh, tel, margin_ax, need64);
                 }
                 cc[a] = 2u * cc[a] + bit;
                 k |= (int)bit << a;
@@ -397,19 +430,11 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     // 4. precision of this boundary
     if (!have64) {
         if (rebase) {
-            te64 = face_t64(r, T, ax, cold + up, r.L);
-            have64 = true;
-            split_local(r, te64, teh, tel);
+            need64();
         } else if (nval.x != r.val.x || nval.y != r.val.y) {
-            const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(r.inv32[ax]);
-            if (r.err + need > P.err_budget) {
-                te64 = face_t64(r, T, ax, cold + up, r.L);
-                have64 = true;
-                split_local(r, te64, teh, tel);
-                r.n_f64 += 1;
-            } else {
-                r.err += need;
-            }
+            const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(r.ih[ax]);
+            if (r.err + need > P.err_budget) need64();
+            else r.err += need;
         }
     }
     // 5. composite the current leaf, then terminate or advance
