@@ -11,7 +11,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcanvox.so")
+# CANVOX_LIB: load the library from another path (for example a build with other compile-time options)
+LIB_PATH = os.environ.get("CANVOX_LIB") or os.path.join(HERE, "libcanvox.so")
 
 OK = 0
 ERR_INVALID_ARG = -1

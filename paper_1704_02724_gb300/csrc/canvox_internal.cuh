@@ -43,6 +43,19 @@ struct View {
     int32_t pad;
 };
 
+// Leaf holding the eye of a view, located once per render by eye_path_kernel.
+// Valid (len > 0) when the eye is inside the canvas and on no cell plane of its
+// path: every ray of the view then starts in this leaf at t = 0 (the ray is on
+// the high side of a plane just after t = 0 iff the eye is above it).
+struct EyePath {
+    int32_t rec[kMaxDepth + 1];  // record of each ancestor level 0 .. len-1
+    uint32_t c[3];               // leaf coordinates at level len
+    int32_t len;                 // leaf level (0: not valid, trace from the root)
+    uint2 val;                   // leaf value (0, 0 = empty)
+    int32_t stored;              // 1 if the leaf has a stored value (slot < 0)
+    int32_t pad[2];
+};
+
 // Counters, in the order of canvox_stats.
 enum Stat {
     kStatRays = 0,
@@ -66,6 +79,7 @@ struct Scratch {
 struct MixedParams {
     Tree tree;
     const View* views;
+    const EyePath* eye;  // one per view
     int32_t n_views;
     int32_t refill;
     int64_t total_rays;  // the queue hands out rays [0, total_rays) ...
@@ -96,6 +110,7 @@ cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out);
 cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 
 // 64-bit element hash shared by the host and device hash of the pools.
 __host__ __device__ inline unsigned long long mix64(unsigned long long z) {

@@ -66,6 +66,7 @@ struct Ctx {
     bool uploaded = false;
     // views: device table and two pinned staging buffers, each guarded by an event
     View* d_views = nullptr;
+    EyePath* d_eye = nullptr;
     int views_cap = 0;
     View* h_views[2] = {nullptr, nullptr};
     cudaEvent_t staged[2] = {nullptr, nullptr};
@@ -98,7 +99,7 @@ void builtin_defaults(canvox_render_opts* o) {
     o->use_graph = 0;
     o->block_threads = 256;
     o->blocks_per_sm = 0;
-    o->refill = 8;
+    o->refill = 0;
     o->smem_records = 0;
     o->frame_levels = 20;
     o->step_limit = 0;
@@ -137,12 +138,15 @@ int ensure_views(int n) {
     if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
     drop_graphs();
     if (g.d_views) cudaFree(g.d_views);
+    if (g.d_eye) cudaFree(g.d_eye);
     for (int b = 0; b < 2; ++b)
         if (g.h_views[b]) cudaFreeHost(g.h_views[b]);
     g.d_views = nullptr;
+    g.d_eye = nullptr;
     g.h_views[0] = g.h_views[1] = nullptr;
     g.views_cap = 0;
     CK(cudaMalloc(&g.d_views, sizeof(View) * (size_t)cap), "cudaMalloc(views)");
+    CK(cudaMalloc(&g.d_eye, sizeof(EyePath) * (size_t)cap), "cudaMalloc(eye paths)");
     for (int b = 0; b < 2; ++b) CK(cudaMallocHost(&g.h_views[b], sizeof(View) * (size_t)cap), "cudaMallocHost(views)");
     g.views_cap = cap;
     return CANVOX_OK;
@@ -258,6 +262,7 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
     CK(cudaMemsetAsync(g.d_scratch, 0, scratch_bytes(queues), s), "cudaMemsetAsync(scratch)");
     const Tree t = device_tree();
     if (o.precision == CANVOX_PREC_MIXED) {
+        CK(launch_eye_paths(t, g.d_views, n, g.d_eye, s), "eye path kernel launch");
         MixedParams p;
         std::memset(&p, 0, sizeof(p));
         p.tree = t;
@@ -272,6 +277,7 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
         p.smem_records = o.smem_records;
         if (!o.per_view) {
             p.views = g.d_views;
+            p.eye = g.d_eye;
             p.n_views = n;
             p.total_rays = total_rays;
             p.ray_base = 0;
@@ -281,6 +287,7 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
         } else {
             for (int v = 0; v < n; ++v) {
                 p.views = g.d_views + v;
+                p.eye = g.d_eye + v;
                 p.n_views = 1;
                 const int64_t rays = (v + 1 < n ? views_host[v + 1].ray_begin : total_rays) - views_host[v].ray_begin;
                 p.total_rays = rays;
@@ -626,6 +633,7 @@ void canvox_release(void) {
     if (g.d_nodes) cudaFree(g.d_nodes);
     if (g.d_leaves) cudaFree(g.d_leaves);
     if (g.d_views) cudaFree(g.d_views);
+    if (g.d_eye) cudaFree(g.d_eye);
     for (int b = 0; b < 2; ++b) {
         if (g.h_views[b]) cudaFreeHost(g.h_views[b]);
         if (g.staged[b]) cudaEventDestroy(g.staged[b]);

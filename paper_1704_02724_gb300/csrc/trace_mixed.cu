@@ -43,6 +43,11 @@ constexpr float kEpsDF = 5.684341886080802e-14f;   // 2^-44: double-float crossi
 constexpr float kEpsDF2 = 1.1368683772161603e-13f; // 2^-43 = 2 * 2^-44: factor 2 of the colour bound
 constexpr int kMaxFrameBits = 22;                   // a frame spans at most 22 levels (exact FP32 planes)
 
+// Resident 256-thread blocks per SM the register allocation must allow (occupancy knob).
+#ifndef CANVOX_MIN_BLOCKS
+#define CANVOX_MIN_BLOCKS 1
+#endif
+
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 __device__ __forceinline__ float hsig(uint2 v) { return __half2float(__ushort_as_half((unsigned short)(v.y >> 16))); }
@@ -211,10 +216,11 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     }
     const View& V = P.views[lo];
     const long long local = (long long)g - V.ray_begin;
-    const long long tile = local >> 5;
+    const unsigned tile = (unsigned)(local >> 5);  // tiles of one view fit 32 bits (width, height < 2^31)
     const int lane = (int)(local & 31);
-    const int i = (int)(tile % V.tiles_x) * kTileW + (lane & (kTileW - 1));
-    const int j = (int)(tile / V.tiles_x) * kTileH + (lane / kTileW);
+    const unsigned ty = tile / (unsigned)V.tiles_x;
+    const int i = (int)(tile - ty * (unsigned)V.tiles_x) * kTileW + (lane & (kTileW - 1));
+    const int j = (int)ty * kTileH + (lane / kTileW);
     if (i >= V.width || j >= V.height) return false;  // padding lane of a ragged tile
     r.view = lo;
     r.pix = V.out_offset + (int64_t)j * V.width + i;
@@ -256,6 +262,22 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     if (miss || !(t0 < t1)) {
         finish(r, P);
         return false;
+    }
+    const EyePath& E = P.eye[r.view];
+    if (E.len > 0 && t0 == 0.0) {
+        // the eye's leaf, located once for the view
+        r.L = E.len;
+        for (int l = 0; l < E.len; ++l) stk[l] = E.rec[l];
+        r.c[0] = E.c[0];
+        r.c[1] = E.c[1];
+        r.c[2] = E.c[2];
+        r.val = E.val;
+        r.n_reads += r.L;
+        r.n_leaf += (uint32_t)E.stored;
+        r.steps = 1;
+        r.f = max(0, r.L - P.frame_levels);
+        set_frame(r, T, inv_extent, t0);
+        return true;
     }
     // locate the leaf that holds r(t0+) from the root, in double-float frames (frame time 0)
     r.c[0] = r.c[1] = r.c[2] = 0u;
@@ -472,7 +494,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-__global__ void __launch_bounds__(256) mixed_kernel(MixedParams P) {
+__global__ void __launch_bounds__(256, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
     int32_t stk[kMaxDepth + 1];
     Ray r;
     r.n_rays = r.n_steps = r.n_reads = r.n_leaf = r.n_rec = r.n_f64 = r.n_rebase = 0;

@@ -181,7 +181,56 @@ __global__ void hash_kernel(Tree t, unsigned long long* out) {
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// One thread per view: the leaf holding the eye, or len = 0 when the eye is
+// outside the canvas or exactly on a mid-plane of its path (then the ray's
+// direction decides the side and every ray locates its own start).
+__global__ void eye_path_kernel(Tree t, const View* views, int n_views, EyePath* out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_views) return;
+    const View& V = views[v];
+    EyePath& E = out[v];
+    E.len = 0;
+    E.stored = 0;
+    E.val = make_uint2(0u, 0u);
+    for (int a = 0; a < 3; ++a)
+        if (!(V.eye[a] >= -t.half && V.eye[a] < t.half)) return;
+    unsigned c[3] = {0u, 0u, 0u};
+    int32_t rec = 0;
+    for (int lev = 0; lev < kMaxDepth; ++lev) {
+        E.rec[lev] = rec;
+        const double w = t.extent * __longlong_as_double((long long)(1023 - (lev + 1)) << 52);
+        int k = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double M = fma((double)(2u * c[a] + 1u), w, -t.half);
+            if (V.eye[a] == M) return;  // on the plane: the direction decides
+            const unsigned b = V.eye[a] > M;
+            c[a] = 2u * c[a] + b;
+            k |= (int)b << a;
+        }
+        const int32_t slot = t.nodes[(long long)rec * 8 + k];
+        if (slot > 0) {
+            rec = slot;
+            continue;
+        }
+        if (slot < 0) {
+            E.val = t.leaves[-(long long)slot - 1];
+            E.stored = 1;
+        }
+        E.c[0] = c[0];
+        E.c[1] = c[1];
+        E.c[2] = c[2];
+        E.len = lev + 1;
+        return;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s) {
+    if (n_views <= 0) return cudaSuccess;
+    eye_path_kernel<<<(n_views + 63) / 64, 64, 0, s>>>(t, views, n_views, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s) {
     if (n_pixels <= 0) return cudaSuccess;

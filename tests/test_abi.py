@@ -55,7 +55,7 @@ def test_struct_layouts_match_header(tmp_path):
 
 def test_host_paths_without_gpu(L):
     d = cx.default_opts()
-    assert d["precision"] == cx.PREC_MIXED and d["frame_levels"] == 20 and d["refill"] == 8
+    assert d["precision"] == cx.PREC_MIXED and d["frame_levels"] == 20 and d["refill"] == 0
     s = cx.get_stats()
     assert s["rays"] == 0
     cams = synth.config_cameras(0)

@@ -70,6 +70,7 @@ def _edge_cameras(extent):
     add([0.25, 0.25, 1.5], [0.25, 0.25, 0.0], 5, 5, tan=0.2)       # on cell planes, axis-aligned
     add([2.0, 2.0, 2.0], [0.0, 0.0, 0.0], 1, 1)                    # single pixel through a corner
     add([3.0, 5.0, 0.0], [3.3, 6.0, 0.2], 8, 4)                    # looks away: all background
+    add([0.25, 0.0, 0.125], [0.4, 0.3, 0.33], 12, 10, tan=1.2)     # eye inside, exactly on three cell planes
     return synth.cameras_array(cams)
 
 
