@@ -55,6 +55,13 @@ __device__ __forceinline__ float hlo(unsigned w) { return __half2float(__ushort_
 __device__ __forceinline__ float hhi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
 __device__ __forceinline__ float finf() { return __int_as_float(0x7F800000); }
 
+// x[a] for a runtime axis without indexing an array (which would put it in local memory).
+template <typename V>
+__device__ __forceinline__ V pick(int a, V x0, V x1, V x2) { return a == 0 ? x0 : (a == 1 ? x1 : x2); }
+
+// (ah, al) < (bh, bl) for normalised double-floats.
+__device__ __forceinline__ bool df_less(float ah, float al, float bh, float bl) { return ah < bh || (ah == bh && al < bl); }
+
 __device__ __forceinline__ int32_t load_slot(const Tree& T, int32_t rec, int k) {
     return __ldg(T.nodes + (int64_t)rec * 8 + k);
 }
@@ -85,10 +92,19 @@ __device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl)
     return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
 }
 
-struct Ray {
+constexpr int kBlock = 256;
+
+// FP64 state and rare counters of a lane: read only by rebases, near-ties and
+// start-up, so it lives in shared memory instead of registers.
+struct Cold {
     double inv64[3], nod64[3];  // t(P) = P inv + nod; axis with d = 0: inv = 0, nod = o
     double tf;                  // FP64 ray parameter at the frame origin
     double invS;                // 1 / frame size
+    uint32_t n_rays, n_steps, n_f64, n_rebase;
+};
+
+struct Ray {
+    Cold* k;
     float ih[3], il[3];         // inv_d as two FP32 words (0 for d = 0)
     float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
     float sf, sf_eps;           // frame size, frame size * 2^-43
@@ -104,40 +120,40 @@ struct Ray {
     int32_t view;
     int64_t pix;
     // counters, summed over every ray the lane traces
-    uint32_t n_rays, n_steps, n_reads, n_leaf, n_rec, n_f64, n_rebase;
+    uint32_t n_reads, n_leaf, n_rec;
 };
 
 __device__ __forceinline__ bool is_zero(const Ray& r, int a) { return (r.zmask >> a) & 1u; }
 
 // Ray on the high side of the global plane x_a = M just after parameter t (FP64).
 __device__ __forceinline__ uint32_t high64(const Ray& r, int a, double M, double t) {
-    if (is_zero(r, a)) return r.nod64[a] >= M;
-    const double tm = fma(M, r.inv64[a], r.nod64[a]);
-    return r.inv64[a] > 0.0 ? (tm <= t) : (tm > t);
+    if (is_zero(r, a)) return r.k->nod64[a] >= M;
+    const double tm = fma(M, r.k->inv64[a], r.k->nod64[a]);
+    return r.k->inv64[a] > 0.0 ? (tm <= t) : (tm > t);
 }
 
 // FP64 crossing time of the face (c + s) of a level-L cell on axis a (exact plane).
 __device__ __forceinline__ double face_t64(const Ray& r, const Tree& T, int a, uint32_t cs, int L) {
     const double P = fma((double)cs, T.extent * pow2d(-L), -T.half);
-    return fma(P, r.inv64[a], r.nod64[a]);
+    return fma(P, r.k->inv64[a], r.k->nod64[a]);
 }
 
 __device__ __forceinline__ void split_local(const Ray& r, double t, float& hi, float& lo) {
-    const double tl = (t - r.tf) * r.invS;
+    const double tl = (t - r.k->tf) * r.k->invS;
     hi = (float)tl;
     lo = (float)(tl - (double)hi);
 }
 
 // Enter the frame at level r.f that holds the cell (r.L, r.c); t = FP64 parameter of the entry.
 __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_extent, double t) {
-    r.tf = t;
+    r.k->tf = t;
     const int sh = r.L - r.f;
     const double Sf = T.extent * pow2d(-r.f);
-    r.invS = pow2d(r.f) * inv_extent;
+    r.k->invS = pow2d(r.f) * inv_extent;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double Fmin = fma((double)(r.c[a] >> sh), Sf, -T.half);
-        const double n = is_zero(r, a) ? (r.nod64[a] - Fmin) * r.invS : (fma(Fmin, r.inv64[a], r.nod64[a]) - t) * r.invS;
+        const double n = is_zero(r, a) ? (r.k->nod64[a] - Fmin) * r.k->invS : (fma(Fmin, r.k->inv64[a], r.k->nod64[a]) - t) * r.k->invS;
         r.nh[a] = (float)n;
         r.nl[a] = (float)(n - (double)r.nh[a]);
     }
@@ -145,7 +161,7 @@ __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_exte
     r.sf_eps = r.sf * kEpsDF2;
     r.cur_hi = 0.0f;
     r.cur_lo = 0.0f;
-    r.n_rebase += 1;
+    r.k->n_rebase += 1;
 }
 
 // Composite the current leaf over [cursor, te]. The length is not clamped at
@@ -176,8 +192,8 @@ __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
     o.w = 1.0f - r.T;
     P.out[r.pix] = o;
     if (P.step_count) P.step_count[r.pix] = r.steps;
-    r.n_rays += 1;
-    r.n_steps += (uint32_t)r.steps;
+    r.k->n_rays += 1;
+    r.k->n_steps += (uint32_t)r.steps;
 }
 
 // Child bit on axis a of the cell at level `lev` with coordinate cc, for the ray
@@ -241,18 +257,18 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         const double da = d[a];
         const double o = V.eye[a];
         if (da != 0.0) {
-            r.inv64[a] = 1.0 / da;
-            r.nod64[a] = -o * r.inv64[a];
-            r.ih[a] = (float)r.inv64[a];
-            r.il[a] = (float)(r.inv64[a] - (double)r.ih[a]);
+            r.k->inv64[a] = 1.0 / da;
+            r.k->nod64[a] = -o * r.k->inv64[a];
+            r.ih[a] = (float)r.k->inv64[a];
+            r.il[a] = (float)(r.k->inv64[a] - (double)r.ih[a]);
             if (da > 0.0) r.dpos |= 1u << a;
-            const double ta = fma(-T.half, r.inv64[a], r.nod64[a]);
-            const double tb = fma(T.half, r.inv64[a], r.nod64[a]);
+            const double ta = fma(-T.half, r.k->inv64[a], r.k->nod64[a]);
+            const double tb = fma(T.half, r.k->inv64[a], r.k->nod64[a]);
             t0 = fmax(t0, da > 0.0 ? ta : tb);
             t1 = fmin(t1, da > 0.0 ? tb : ta);
         } else {
-            r.inv64[a] = 0.0;
-            r.nod64[a] = o;
+            r.k->inv64[a] = 0.0;
+            r.k->nod64[a] = o;
             r.ih[a] = 0.0f;
             r.il[a] = 0.0f;
             r.zmask |= 1u << a;
@@ -336,26 +352,39 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     const int kf = r.L - r.f;
     const float sc = pow2f(-kf);
     const uint32_t fmask = (1u << kf) - 1u;
-    float th[3], tl[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (is_zero(r, a)) {
-            th[a] = finf();
-            tl[a] = 0.0f;
-        } else {
-            const uint32_t rel = (r.c[a] & fmask) + ((r.dpos >> a) & 1u);
-            df_cross((float)rel * sc, r.ih[a], r.il[a], r.nh[a], r.nl[a], th[a], tl[a]);
-        }
+    float th0, tl0, th1, tl1, th2, tl2;
+#define CANVOX_EXIT_T(a, H, L_)                                                                    \
+    if (is_zero(r, a)) {                                                                           \
+        H = finf();                                                                                \
+        L_ = 0.0f;                                                                                 \
+    } else {                                                                                       \
+        const uint32_t rel = (r.c[a] & fmask) + ((r.dpos >> (a)) & 1u);                            \
+        df_cross((float)rel * sc, r.ih[a], r.il[a], r.nh[a], r.nl[a], H, L_);                      \
     }
+    CANVOX_EXIT_T(0, th0, tl0)
+    CANVOX_EXIT_T(1, th1, tl1)
+    CANVOX_EXIT_T(2, th2, tl2)
+#undef CANVOX_EXIT_T
+    // exit axis: smallest time, ties to the lowest axis; and the runner-up
     int ax = 0;
-    if (th[1] < th[ax] || (th[1] == th[ax] && tl[1] < tl[ax])) ax = 1;
-    if (th[2] < th[ax] || (th[2] == th[ax] && tl[2] < tl[ax])) ax = 2;
-    const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
-    const int a2 = (th[b2] < th[b1] || (th[b2] == th[b1] && tl[b2] < tl[b1])) ? b2 : b1;
-    float teh = th[ax], tel = tl[ax];
+    float teh = th0, tel = tl0;
+    if (df_less(th1, tl1, teh, tel)) { ax = 1; teh = th1; tel = tl1; }
+    if (df_less(th2, tl2, teh, tel)) { ax = 2; teh = th2; tel = tl2; }
+    float sh2, sl2;
+    int a2;
+    {
+        const float ph = ax == 0 ? th1 : th0, pl = ax == 0 ? tl1 : tl0;
+        const float qh = ax == 2 ? th1 : th2, ql = ax == 2 ? tl1 : tl2;
+        const int pa = ax == 0 ? 1 : 0, qa = ax == 2 ? 1 : 2;
+        const bool q = df_less(qh, ql, ph, pl);
+        sh2 = q ? qh : ph;
+        sl2 = q ? ql : pl;
+        a2 = q ? qa : pa;
+    }
+    float inv_ax = pick(ax, r.ih[0], r.ih[1], r.ih[2]);
     bool have64 = false;
     double te64 = 0.0;
-    if (df_diff(th[a2], tl[a2], th[ax], tl[ax]) <= kEpsDF * (fabsf(r.ih[ax]) + fabsf(r.ih[a2]))) {
+    if (df_diff(sh2, sl2, teh, tel) <= kEpsDF * (fabsf(inv_ax) + fabsf(pick(a2, r.ih[0], r.ih[1], r.ih[2])))) {
         // the exit face is ambiguous (ray within the bound of an edge): decide in FP64
         double best = __longlong_as_double(0x7FF0000000000000ll);
         int bax = 0;
@@ -366,14 +395,15 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             if (ta < best) { best = ta; bax = a; }
         }
         ax = bax;
+        inv_ax = pick(ax, r.ih[0], r.ih[1], r.ih[2]);
         te64 = best;
         have64 = true;
         split_local(r, te64, teh, tel);
-        r.n_f64 += 1;
+        r.k->n_f64 += 1;
     }
     // 2. neighbour across the exit face
     const uint32_t up = (r.dpos >> ax) & 1u;
-    const uint32_t cold = r.c[ax];
+    const uint32_t cold = pick(ax, r.c[0], r.c[1], r.c[2]);
     const uint32_t cn = up ? cold + 1u : cold - 1u;
     const int Lold = r.L;
     auto need64 = [&]() {
@@ -381,14 +411,14 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             te64 = face_t64(r, T, ax, cold + up, Lold);
             have64 = true;
             split_local(r, te64, teh, tel);
-            r.n_f64 += 1;
+            r.k->n_f64 += 1;
         }
         return te64;
     };
     if ((cn >> r.L) != 0u) {
         // leaving the canvas: last segment, bounded like a boundary to sigma = 0
         if (!have64 && (r.val.y >> 16)) {
-            const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(r.ih[ax]);
+            const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(inv_ax);
             if (r.err + need > P.err_budget) need64();
             else r.err += need;
         }
@@ -400,13 +430,12 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     const bool fexit = lstar < r.f;
     if (fexit) need64();
     // 3. re-descend from the common ancestor
-    uint32_t cc[3] = {r.c[0], r.c[1], r.c[2]};
-    cc[ax] = cn;
+    uint32_t cc[3] = {ax == 0 ? cn : r.c[0], ax == 1 ? cn : r.c[1], ax == 2 ? cn : r.c[2]};
     int Lc = r.L;
     int lev = lstar;
     int32_t rec = stk[lstar];
     int32_t slot;
-    const float margin_ax = kEpsDF * fabsf(r.ih[ax]);
+    const float margin_ax = kEpsDF * fabsf(inv_ax);
     for (;;) {
         int k;
         if (lev < Lc) {
@@ -454,7 +483,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         if (rebase) {
             need64();
         } else if (nval.x != r.val.x || nval.y != r.val.y) {
-            const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(r.ih[ax]);
+            const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(inv_ax);
             if (r.err + need > P.err_budget) need64();
             else r.err += need;
         }
@@ -494,10 +523,13 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-__global__ void __launch_bounds__(256, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
+__global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
+    __shared__ Cold cold[kBlock];
     int32_t stk[kMaxDepth + 1];
     Ray r;
-    r.n_rays = r.n_steps = r.n_reads = r.n_leaf = r.n_rec = r.n_f64 = r.n_rebase = 0;
+    r.k = &cold[threadIdx.x];
+    r.k->n_rays = r.k->n_steps = r.k->n_f64 = r.k->n_rebase = 0;
+    r.n_reads = r.n_leaf = r.n_rec = 0;
     const double inv_extent = 1.0 / P.tree.extent;
     const unsigned lane = threadIdx.x & 31u;
     bool alive = false;
@@ -526,7 +558,7 @@ __global__ void __launch_bounds__(256, CANVOX_MIN_BLOCKS) mixed_kernel(MixedPara
             busy = __ballot_sync(kFull, alive);
         } while (busy != 0u && (drained || __popc(busy) > P.refill));
     }
-    const unsigned long long v[7] = {r.n_rays, r.n_steps, r.n_reads, r.n_leaf, r.n_rec, r.n_f64, r.n_rebase};
+    const unsigned long long v[7] = {r.k->n_rays, r.k->n_steps, r.n_reads, r.n_leaf, r.n_rec, r.k->n_f64, r.k->n_rebase};
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         const unsigned long long s = warp_sum(v[i]);
