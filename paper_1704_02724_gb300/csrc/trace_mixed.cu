@@ -45,14 +45,25 @@ constexpr int kMaxFrameBits = 22;                   // a frame spans at most 22 
 
 // Resident 256-thread blocks per SM the register allocation must allow (occupancy knob).
 #ifndef CANVOX_MIN_BLOCKS
-#define CANVOX_MIN_BLOCKS 1
+#define CANVOX_MIN_BLOCKS 3
 #endif
 
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
-__device__ __forceinline__ float hsig(uint2 v) { return __half2float(__ushort_as_half((unsigned short)(v.y >> 16))); }
-__device__ __forceinline__ float hlo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
-__device__ __forceinline__ float hhi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+// IEEE binary16 bits -> float, exactly, on the integer and FP32 pipes (no conversion
+// instruction): the 15 magnitude bits shifted to the FP32 field positions read as
+// 2^-112 times the value (normals and subnormals alike); the sign is copied.
+__device__ __forceinline__ float half_bits_to_float(unsigned h) {
+    const float m = __int_as_float((int)((h & 0x7FFFu) << 13)) * 5.192296858534828e+33f;  // * 2^112
+    return __int_as_float(__float_as_int(m) | (int)((h & 0x8000u) << 16));
+}
+__device__ __forceinline__ float hsig(uint2 v) { return half_bits_to_float(v.y >> 16); }
+__device__ __forceinline__ float hlo(unsigned w) { return half_bits_to_float(w & 0xFFFFu); }
+__device__ __forceinline__ float hhi(unsigned w) { return half_bits_to_float(w >> 16); }
+// (float)x for x < 2^23, exactly, without a conversion instruction.
+__device__ __forceinline__ float small_uint_to_float(uint32_t x) {
+    return __fsub_rn(__int_as_float((int)(0x4B000000u | x)), 8388608.0f);
+}
 __device__ __forceinline__ float finf() { return __int_as_float(0x7F800000); }
 
 // x[a] for a runtime axis without indexing an array (which would put it in local memory).
@@ -204,7 +215,7 @@ __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a
                                               float tl, float margin_t, Need64 need64) {
     if (lev - r.f < kMaxFrameBits) {
         const uint32_t rel = cc & ((1u << (lev - r.f)) - 1u);
-        const float Mp = (float)(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
+        const float Mp = small_uint_to_float(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
         if (is_zero(r, a)) {
             const float dm = __fadd_rn(__fsub_rn(r.nh[a], Mp), r.nl[a]);
             if (fabsf(dm) > kEpsDF) return dm >= 0.0f;
@@ -359,7 +370,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         L_ = 0.0f;                                                                                 \
     } else {                                                                                       \
         const uint32_t rel = (r.c[a] & fmask) + ((r.dpos >> (a)) & 1u);                            \
-        df_cross((float)rel * sc, r.ih[a], r.il[a], r.nh[a], r.nl[a], H, L_);                      \
+        df_cross(small_uint_to_float(rel) * sc, r.ih[a], r.il[a], r.nh[a], r.nl[a], H, L_);          \
     }
     CANVOX_EXIT_T(0, th0, tl0)
     CANVOX_EXIT_T(1, th1, tl1)
