@@ -167,6 +167,30 @@ int canvox_render_ex(const canvox_camera* cams, int32_t n_views, float* out_rgba
 int canvox_render_host(const canvox_camera* cams, int32_t n_views, float* out_rgba_host, void* stream,
                        const canvox_render_opts* opts);
 
+/*
+ * Render without allocating anything (the paper has no counterpart: this is
+ * an interface for callers that cannot call cudaMalloc, such as code inside a
+ * memory pool that owns all device memory, or a real-time loop that must not
+ * touch the allocator). The caller passes its own device buffers:
+ *   node_pool_dev, n_records, leaf_rgba_dev, n_leaves, depth, extent : the
+ *       canvas in the layout of canvox_upload_octree, already in device memory
+ *       and already valid under its rules (this call does not validate the
+ *       pools; an invalid pool reads out of bounds);
+ *   cams, n_views (0..64) : host camera records, as for canvox_render;
+ *   out_rgba_dev, stream : as for canvox_render (asynchronous, stream-ordered).
+ * Default options, no counters (canvox_get_stats does not see these calls).
+ * The working memory (counters, ray-queue head, view table, eye paths) is one
+ * fixed 24 KiB array in device global memory that every GPU loading the
+ * library holds until the process exits. The first call on a device looks up
+ * that array's device address, so make it before any stream capture. All
+ * calls share the array: calls that overlap on the GPU race, so serialise
+ * them (one stream, or wait between them). More than 64 views:
+ * CANVOX_ERR_INVALID_ARG.
+ */
+int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_records, const uint16_t* leaf_rgba_dev,
+                          int64_t n_leaves, int32_t depth, double extent, const canvox_camera* cams,
+                          int32_t n_views, float* out_rgba_dev, void* stream);
+
 /* Counters of the last render (synchronises with the library's work). */
 int canvox_get_stats(canvox_stats* s);
 

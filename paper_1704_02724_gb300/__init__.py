@@ -15,6 +15,7 @@ from .canvox import (  # noqa: F401
     upload_octree,
     render,
     render_host,
+    render_noalloc,
     get_stats,
     octree_hash,
     autotune,

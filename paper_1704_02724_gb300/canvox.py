@@ -81,6 +81,8 @@ def lib():
         L.canvox_render_ex.restype = ctypes.c_int
         L.canvox_render_host.argtypes = [vp, i32, vp, vp, ctypes.POINTER(Opts)]
         L.canvox_render_host.restype = ctypes.c_int
+        L.canvox_render_noalloc.argtypes = [vp, i64, vp, i64, i32, ctypes.c_double, vp, i32, vp, vp]
+        L.canvox_render_noalloc.restype = ctypes.c_int
         L.canvox_get_stats.argtypes = [ctypes.POINTER(Stats)]
         L.canvox_get_stats.restype = ctypes.c_int
         L.canvox_octree_hash.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
@@ -179,6 +181,14 @@ def render_host(cams, out, stream=None, **opts):
         ptr = int(out.data_ptr())
     _check(lib().canvox_render_host(cams.ctypes.data if cams.size else None, cams.shape[0], ptr,
                                     _stream_ptr(stream), ctypes.byref(o)))
+
+
+def render_noalloc(nodes_dev, n_records, leaves_dev, n_leaves, depth, extent, cams, out, stream=None):
+    """canvox_render_noalloc: caller-owned device pools and image, no allocation by the library."""
+    cams = _cams(cams)
+    _check(lib().canvox_render_noalloc(_dev_ptr(nodes_dev), int(n_records), _dev_ptr(leaves_dev), int(n_leaves),
+                                       int(depth), float(extent), cams.ctypes.data if cams.size else None,
+                                       cams.shape[0], _dev_ptr(out), _stream_ptr(stream)))
 
 
 def get_stats(check=True):

@@ -112,6 +112,12 @@ cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 
+// Host helpers of runtime.cu shared with other entry points.
+int build_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays);
+void builtin_render_opts(canvox_render_opts* o);
+int set_error(int code, const char* msg);
+void clear_error();
+
 // 64-bit element hash shared by the host and device hash of the pools.
 __host__ __device__ inline unsigned long long mix64(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -320,6 +320,15 @@ bool same_opts(const canvox_render_opts& a, const canvox_render_opts& b) { retur
 
 }  // namespace
 
+namespace canvox {
+int build_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays) {
+    return setup_views(cams, n, out, total_rays);
+}
+void builtin_render_opts(canvox_render_opts* o) { builtin_defaults(o); }
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+void clear_error() { g_err.clear(); }
+}  // namespace canvox
+
 extern "C" {
 
 void canvox_default_opts(canvox_render_opts* o) {
