@@ -83,8 +83,10 @@ typedef struct canvox_camera {
  *   block_threads : threads per block of the persistent kernel (multiple of 32, 32..256).
  *   blocks_per_sm : persistent blocks per SM (the grid is SMs x this).
  *   refill        : a warp refetches rays when at most this many lanes are still busy (0..31).
- *   smem_records  : records of the breadth-first tree prefix kept in shared memory (0 = none).
- *   frame_levels  : K, the most levels a local FP32 frame may sit above its cell (1..22).
+ *   smem_records  : records of the breadth-first tree prefix (the top of the tree) copied to shared
+ *                   memory at kernel start (0 = none, at most 6144; blocks per SM shrink to fit).
+ *   frame_levels  : K, the most levels a local frame may sit above its cell (1..22).
+ *   tile_w        : pixel tile a warp starts with: tile_w x (32 / tile_w), tile_w in {4, 8, 16, 32}.
  *   step_limit    : most leaves one ray may visit (0 = 3 * 2^depth + 8, capped at 2^31 - 1).
  *   t_min         : stop a ray once its transmittance is below this (< 0: default 2^-20).
  *   err_budget    : per-ray bound on the colour error the FP32 boundaries may add before
@@ -100,6 +102,7 @@ typedef struct canvox_render_opts {
     int32_t refill;
     int32_t smem_records;
     int32_t frame_levels;
+    int32_t tile_w;
     int64_t step_limit;
     float t_min;
     float err_budget;
@@ -198,9 +201,9 @@ int canvox_get_stats(canvox_stats* s);
 int canvox_octree_hash(uint64_t* host_hash, uint64_t* device_hash);
 
 /*
- * Time a grid of schedules (block size, blocks per SM, refill threshold,
- * shared-memory prefix, frame levels) on these views and keep the fastest as
- * the default options. Synchronous. Writes the chosen options to *best when
+ * Search the schedule (block size, refill threshold, tile shape, shared-memory
+ * prefix, frame levels; one parameter at a time, two passes) by timing renders
+ * of these views, and keep the fastest as the default options. Synchronous. Writes the chosen options to *best when
  * best is not NULL.
  */
 int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, canvox_render_opts* best);

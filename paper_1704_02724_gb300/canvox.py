@@ -47,6 +47,7 @@ class Opts(ctypes.Structure):
         ("refill", ctypes.c_int32),
         ("smem_records", ctypes.c_int32),
         ("frame_levels", ctypes.c_int32),
+        ("tile_w", ctypes.c_int32),
         ("step_limit", ctypes.c_int64),
         ("t_min", ctypes.c_float),
         ("err_budget", ctypes.c_float),

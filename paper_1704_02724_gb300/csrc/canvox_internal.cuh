@@ -8,12 +8,11 @@
 
 namespace canvox {
 
-// Rays are handed out in tiles of 8 x 4 pixels (one warp); a view of W x H
-// pixels has ceil(W/8) x ceil(H/4) tiles, ray g of the launch is lane g % 32 of
-// tile g / 32.
-constexpr int kTileW = 8;
-constexpr int kTileH = 4;
+// Rays are handed out in tiles of tw x th = 32 pixels (one warp; tw = 2^tile_wl);
+// a view of W x H pixels has ceil(W/tw) x ceil(H/th) tiles, and ray g of the
+// launch is lane g % 32 of tile g / 32.
 constexpr int kMaxDepth = 30;
+constexpr int kMaxSmemRecords = 6144;
 
 // Device view of the uploaded canvas.
 struct Tree {
@@ -40,7 +39,7 @@ struct View {
     int64_t ray_begin;  // first ray index of this view in the launch (multiple of 32)
     int32_t width, height;
     int32_t tiles_x;
-    int32_t pad;
+    int32_t tile_wl;  // log2 of the tile width
 };
 
 // Leaf holding the eye of a view, located once per render by eye_path_kernel.
@@ -106,14 +105,14 @@ struct PlainParams {
 };
 
 // Launchers (trace_mixed.cu, trace_plain.cu, runtime.cu).
-cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s);
+cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s);  // smem from p.smem_records
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out);
 cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 
 // Host helpers of runtime.cu shared with other entry points.
-int build_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays);
+int build_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t* total_rays);
 void builtin_render_opts(canvox_render_opts* o);
 int set_error(int code, const char* msg);
 void clear_error();

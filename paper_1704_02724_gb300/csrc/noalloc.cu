@@ -70,10 +70,10 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
     }
     View hv[kNoallocMaxViews];  // host stack, no heap
     int64_t total_rays = 0;
-    int rc = build_views(cams, n_views, hv, &total_rays);
-    if (rc) return rc;
     canvox_render_opts o;
     builtin_render_opts(&o);
+    int rc = build_views(cams, n_views, o.tile_w, hv, &total_rays);
+    if (rc) return rc;
     unsigned char* base = nullptr;
     rc = scratch_address(&base);
     if (rc) return rc;

@@ -102,6 +102,7 @@ void builtin_defaults(canvox_render_opts* o) {
     o->refill = 0;
     o->smem_records = 0;
     o->frame_levels = 20;
+    o->tile_w = 8;
     o->step_limit = 0;
     o->t_min = -1.0f;
     o->err_budget = 3.0e-6f;
@@ -171,7 +172,9 @@ bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]
 double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 // Per-view set-up in FP64: Gram-Schmidt frame from forward, pixel scale factors, tiling.
-int setup_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays) {
+int setup_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t* total_rays) {
+    const int wl = tile_w == 4 ? 2 : tile_w == 8 ? 3 : tile_w == 16 ? 4 : 5;
+    const int tw = 1 << wl, th = 32 >> wl;
     int64_t ray = 0;
     for (int v = 0; v < n; ++v) {
         const canvox_camera& c = cams[v];
@@ -205,8 +208,9 @@ int setup_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays
         V.out_offset = c.out_offset_px;
         V.width = c.width;
         V.height = c.height;
-        V.tiles_x = (c.width + kTileW - 1) / kTileW;
-        const int64_t tiles = (int64_t)V.tiles_x * ((c.height + kTileH - 1) / kTileH);
+        V.tiles_x = (c.width + tw - 1) / tw;
+        V.tile_wl = wl;
+        const int64_t tiles = (int64_t)V.tiles_x * ((c.height + th - 1) / th);
         V.ray_begin = ray;
         ray += tiles * 32;
     }
@@ -226,6 +230,11 @@ int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (o->frame_levels < 1 || o->frame_levels > 22) return fail(CANVOX_ERR_INVALID_ARG, "frame_levels %d (1..22)", o->frame_levels);
     if (o->blocks_per_sm < 0 || o->smem_records < 0 || o->step_limit < 0)
         return fail(CANVOX_ERR_INVALID_ARG, "negative schedule option");
+    if (o->smem_records > kMaxSmemRecords) return fail(CANVOX_ERR_INVALID_ARG, "smem_records %d (at most 6144)", o->smem_records);
+    if (o->smem_records > g.n_rec) o->smem_records = (int32_t)g.n_rec;
+    if (o->tile_w == 0) o->tile_w = 8;
+    if (o->tile_w != 4 && o->tile_w != 8 && o->tile_w != 16 && o->tile_w != 32)
+        return fail(CANVOX_ERR_INVALID_ARG, "tile_w %d (4, 8, 16 or 32)", o->tile_w);
     if (!(o->err_budget >= 0.0f) || !std::isfinite(o->err_budget)) return fail(CANVOX_ERR_INVALID_ARG, "err_budget");
     if (!std::isfinite(o->t_min)) return fail(CANVOX_ERR_INVALID_ARG, "t_min");
     if (o->t_min < 0.0f) o->t_min = 9.5367431640625e-07f;  // 2^-20
@@ -235,7 +244,7 @@ int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     }
     if (o->blocks_per_sm == 0) {
         int b = 0;
-        CK(mixed_max_blocks_per_sm(o->block_threads, 0, &b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        CK(mixed_max_blocks_per_sm(o->block_threads, o->smem_records * 32, &b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         o->blocks_per_sm = b > 0 ? b : 1;
     }
     return CANVOX_OK;
@@ -321,8 +330,8 @@ bool same_opts(const canvox_render_opts& a, const canvox_render_opts& b) { retur
 }  // namespace
 
 namespace canvox {
-int build_views(const canvox_camera* cams, int n, View* out, int64_t* total_rays) {
-    return setup_views(cams, n, out, total_rays);
+int build_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t* total_rays) {
+    return setup_views(cams, n, tile_w, out, total_rays);
 }
 void builtin_render_opts(canvox_render_opts* o) { builtin_defaults(o); }
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -452,7 +461,7 @@ int canvox_render_ex(const canvox_camera* cams, int32_t n_views, float* out_rgba
     if (n_views == 0) return CANVOX_OK;
     std::vector<View> views((size_t)n_views);
     int64_t total_rays = 0;
-    rc = setup_views(cams, n_views, views.data(), &total_rays);
+    rc = setup_views(cams, n_views, o.tile_w, views.data(), &total_rays);
     if (rc) return rc;
     if ((rc = ensure_views(n_views)) || (rc = ensure_scratch(o.per_view ? n_views : 1))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -591,39 +600,48 @@ int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, ca
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    canvox_render_opts base;
-    builtin_defaults(&base);
-    canvox_render_opts win = base;
-    float best_ms = 1e30f;
-    const int blocks[] = {128, 256};
-    const int refills[] = {0, 4, 8, 16, 24};
-    const int frames[] = {8, 12, 16};
     int rc = CANVOX_OK;
-    for (int bt : blocks)
-        for (int rf : refills)
-            for (int fl : frames) {
-                canvox_render_opts o = base;
-                o.block_threads = bt;
-                o.refill = rf;
-                o.frame_levels = fl;
+    // time one schedule: best of 2 renders after one warm-up
+    auto time_opts = [&](const canvox_render_opts& o) -> float {
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && rc == CANVOX_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = canvox_render_ex(cams, n_views, reinterpret_cast<float*>(out), stream, &o);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < ms_min) ms_min = ms;
+        }
+        return ms_min;
+    };
+    canvox_render_opts win;
+    builtin_defaults(&win);
+    float best_ms = time_opts(win);
+    const int blocks[] = {128, 256};
+    const int refills[] = {0, 2, 4};
+    const int tiles[] = {4, 8, 16, 32};
+    const int smems[] = {0, 256, 1024, 4096};
+    const int frames[] = {16, 20, 22};
+    for (int pass = 0; pass < 2 && rc == CANVOX_OK; ++pass) {
+        for (int which = 0; which < 5 && rc == CANVOX_OK; ++which) {
+            const int* vals = which == 0 ? blocks : which == 1 ? refills : which == 2 ? tiles : which == 3 ? smems : frames;
+            const int nv = which == 0 ? 2 : which == 1 ? 3 : which == 2 ? 4 : which == 3 ? 4 : 3;
+            for (int i = 0; i < nv && rc == CANVOX_OK; ++i) {
+                canvox_render_opts o = win;
+                int* field = which == 0 ? &o.block_threads : which == 1 ? &o.refill : which == 2 ? &o.tile_w
+                             : which == 3 ? &o.smem_records : &o.frame_levels;
+                if (*field == vals[i]) continue;
+                *field = vals[i];
                 o.blocks_per_sm = 0;
-                float ms_min = 1e30f;
-                for (int rep = 0; rep < 3 && rc == CANVOX_OK; ++rep) {
-                    cudaEventRecord(e0, s);
-                    rc = canvox_render_ex(cams, n_views, reinterpret_cast<float*>(out), stream, &o);
-                    cudaEventRecord(e1, s);
-                    cudaEventSynchronize(e1);
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0 && ms < ms_min) ms_min = ms;
-                }
-                if (rc) break;
-                if (ms_min < best_ms) {
-                    best_ms = ms_min;
+                const float ms = time_opts(o);
+                if (rc == CANVOX_OK && ms < best_ms) {
+                    best_ms = ms;
                     win = o;
-                    win.blocks_per_sm = 0;
                 }
             }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);

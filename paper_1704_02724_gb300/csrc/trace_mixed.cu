@@ -73,7 +73,10 @@ __device__ __forceinline__ V pick(int a, V x0, V x1, V x2) { return a == 0 ? x0 
 // (ah, al) < (bh, bl) for normalised double-floats.
 __device__ __forceinline__ bool df_less(float ah, float al, float bh, float bl) { return ah < bh || (ah == bh && al < bl); }
 
-__device__ __forceinline__ int32_t load_slot(const Tree& T, int32_t rec, int k) {
+// Child slot k of record rec: from the shared-memory copy of the tree's breadth-first prefix when the
+// record is in it (records [0, n_smem)), else through the read-only data cache.
+__device__ __forceinline__ int32_t load_slot(const Tree& T, const int32_t* s_nodes, int32_t n_smem, int32_t rec, int k) {
+    if (rec < n_smem) return s_nodes[rec * 8 + k];
     return __ldg(T.nodes + (int64_t)rec * 8 + k);
 }
 __device__ __forceinline__ uint2 load_leaf(const Tree& T, int32_t slot) { return __ldg(T.leaves + (-(int64_t)slot - 1)); }
@@ -116,6 +119,8 @@ struct Cold {
 
 struct Ray {
     Cold* k;
+    const int32_t* s_nodes;  // shared-memory copy of the first n_smem records
+    int32_t n_smem;
     float ih[3], il[3];         // inv_d as two FP32 words (0 for d = 0)
     float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
     float sf, sf_eps;           // frame size, frame size * 2^-43
@@ -246,8 +251,9 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     const unsigned tile = (unsigned)(local >> 5);  // tiles of one view fit 32 bits (width, height < 2^31)
     const int lane = (int)(local & 31);
     const unsigned ty = tile / (unsigned)V.tiles_x;
-    const int i = (int)(tile - ty * (unsigned)V.tiles_x) * kTileW + (lane & (kTileW - 1));
-    const int j = (int)ty * kTileH + (lane / kTileW);
+    const int wl = V.tile_wl;
+    const int i = ((int)(tile - ty * (unsigned)V.tiles_x) << wl) + (lane & ((1 << wl) - 1));
+    const int j = (int)ty * (32 >> wl) + (lane >> wl);
     if (i >= V.width || j >= V.height) return false;  // padding lane of a ragged tile
     r.view = lo;
     r.pix = V.out_offset + (int64_t)j * V.width + i;
@@ -330,7 +336,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
             r.c[a] = 2u * r.c[a] + b;
             k |= (int)b << a;
         }
-        slot = load_slot(T, rec, k);
+        slot = load_slot(T, r.s_nodes, r.n_smem, rec, k);
         r.n_rec += 1;
         if (slot > 0) {
             ++lev;
@@ -471,7 +477,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             }
             ++Lc;
         }
-        slot = load_slot(T, rec, k);
+        slot = load_slot(T, r.s_nodes, r.n_smem, rec, k);
         r.n_rec += 1;
         if (slot > 0) {
             ++lev;
@@ -536,9 +542,14 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 
 __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
     __shared__ Cold cold[kBlock];
+    extern __shared__ int32_t s_nodes[];
+    for (int i = threadIdx.x; i < P.smem_records * 8; i += blockDim.x) s_nodes[i] = __ldg(P.tree.nodes + i);
+    __syncthreads();
     int32_t stk[kMaxDepth + 1];
     Ray r;
     r.k = &cold[threadIdx.x];
+    r.s_nodes = s_nodes;
+    r.n_smem = P.smem_records;
     r.k->n_rays = r.k->n_steps = r.k->n_f64 = r.k->n_rebase = 0;
     r.n_reads = r.n_leaf = r.n_rec = 0;
     const double inv_extent = 1.0 / P.tree.extent;
@@ -580,11 +591,20 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
 }  // namespace
 
 cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s) {
-    mixed_kernel<<<grid, block, 0, s>>>(p);
+    const int smem = p.smem_records * 32;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    mixed_kernel<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out) {
+    if (smem_bytes > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel, block, smem_bytes);
 }
 

@@ -13,8 +13,10 @@ for config 0, metres for configs 1-4. Extinction sigma is per canvas unit.
       (c1 extinction recipe, kept 10 m clear of the rooms) plus 200,000 fine spheres r log-U[2.4 mm, 10 cm]
       in four 1 m room boxes, extinction from an optical thickness 2 r sigma log-U[0.002, 0.2];
       stereo pair 2160x2160 per eye, 90 deg, eye separation 64 mm, head inside room 0.
-  c3  depth 27, 40 km canvas (finest 0.3 mm): recipe of c2 with 1,000,000 fine spheres
-      r log-U[0.3 mm, 10 cm]; 8 stereo pairs (4 rooms x scales 1 and 0.01).
+  c3  depth 27, 40 km canvas (finest 0.3 mm): recipe of c2 with fine spheres r log-U[0.3 mm, 10 cm];
+      8 stereo pairs (4 rooms x scales 1 and 0.01). 100,000 fine spheres by default: with ten cells
+      per brush radius each fine sphere adds about 3,300 leaves at depth 27, so the 1,000,000 of the
+      workload description would need about 3.3e9 leaves, beyond 32-bit leaf indices.
   c4  the c3 canvas; 64 views, square side log-U[256, 2160], camera scale log-U[1 mm, 10 km].
 """
 import math
@@ -120,7 +122,7 @@ def build_config(cid, n_fine=None):
         c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 200_000, E / 2.0 ** D)
     elif cid in (3, 4):
         rng = Rng(SEED_BASE + 3)
-        c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 1_000_000, E / 2.0 ** D)
+        c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 100_000, E / 2.0 ** D)
     else:
         raise KeyError(cid)
     cv = stamp_canvas(D, E, c, r, q)

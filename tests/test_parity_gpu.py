@@ -151,7 +151,7 @@ def _sample_pixels(cams, n_random, n_tiles, seed):
     return np.array(sorted(idx), dtype=np.int64)
 
 
-@pytest.mark.parametrize("cid,n_random", [(1, 100000), (2, 300000)])
+@pytest.mark.parametrize("cid,n_random", [(1, 100000), (2, 300000), (3, 200000), (4, 200000)])
 def test_full_size_sampled(cid, n_random):
     """Full-size images in the benchmark's launch configuration; oracle on sampled pixels."""
     cv = config_canvas(cid)
@@ -170,9 +170,32 @@ def test_schedules_agree_bitwise():
     cams = _edge_cameras(1.0)
     base, _ = render(cv, cams, key="c0")
     for kw in (dict(per_view=1), dict(use_graph=1), dict(use_graph=1), dict(refill=0, block_threads=128),
-               dict(refill=31, blocks_per_sm=1)):
+               dict(refill=31, blocks_per_sm=1), dict(tile_w=4), dict(tile_w=32, refill=2), dict(tile_w=16),
+               dict(smem_records=100), dict(smem_records=6144, block_threads=128), dict(frame_levels=1),
+               dict(frame_levels=22)):
         img, _ = render(cv, cams, key="c0", **kw)
         np.testing.assert_array_equal(img, base, err_msg=str(kw))
+
+
+def test_frame_levels_do_not_change_depth27_pixels():
+    """Frames of 1 to 22 levels give the same image within the bar on the depth-27 canvas (precision pin)."""
+    cv = config_canvas(3)
+    cams = synth.config_cameras(3, res_scale=0.05)
+    ref = oracle.render(cv, cams)
+    for K in (1, 8, 22):
+        img, st = render(cv, cams, key="c3", frame_levels=K)
+        assert max_err(img, ref) <= TOL, K
+
+
+def test_autotune_keeps_results():
+    cv = config_canvas(0)
+    cams = _edge_cameras(1.0)
+    base, _ = render(cv, cams, key="c0")
+    best = cx.autotune(cams)
+    assert best["tile_w"] in (4, 8, 16, 32) and best["block_threads"] in (128, 256)
+    assert cx.default_opts()["tile_w"] == best["tile_w"]
+    img, _ = render(cv, cams, key="c0")
+    np.testing.assert_array_equal(img, base)
 
 
 def test_render_host_matches_device():
