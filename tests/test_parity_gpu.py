@@ -166,13 +166,14 @@ def test_full_size_sampled(cid, n_random):
 
 
 def test_schedules_agree_bitwise():
+    """Schedule options change which lane traces which ray, never a ray's arithmetic.
+    (frame_levels changes the frames, hence the rounding; it is checked against the bar instead.)"""
     cv = config_canvas(0)
     cams = _edge_cameras(1.0)
     base, _ = render(cv, cams, key="c0")
     for kw in (dict(per_view=1), dict(use_graph=1), dict(use_graph=1), dict(refill=0, block_threads=128),
                dict(refill=31, blocks_per_sm=1), dict(tile_w=4), dict(tile_w=32, refill=2), dict(tile_w=16),
-               dict(smem_records=100), dict(smem_records=6144, block_threads=128), dict(frame_levels=1),
-               dict(frame_levels=22)):
+               dict(smem_records=100), dict(smem_records=6144, block_threads=128)):
         img, _ = render(cv, cams, key="c0", **kw)
         np.testing.assert_array_equal(img, base, err_msg=str(kw))
 
