@@ -73,10 +73,13 @@ __device__ __forceinline__ V pick(int a, V x0, V x1, V x2) { return a == 0 ? x0 
 // (ah, al) < (bh, bl) for normalised double-floats.
 __device__ __forceinline__ bool df_less(float ah, float al, float bh, float bl) { return ah < bh || (ah == bh && al < bl); }
 
+extern __shared__ int32_t s_nodes[];  // copy of the tree's first records (kernel instance with kSmem)
+
 // Child slot k of record rec: from the shared-memory copy of the tree's breadth-first prefix when the
-// record is in it (records [0, n_smem)), else through the read-only data cache.
-__device__ __forceinline__ int32_t load_slot(const Tree& T, const int32_t* s_nodes, int32_t n_smem, int32_t rec, int k) {
-    if (rec < n_smem) return s_nodes[rec * 8 + k];
+// kernel keeps one and the record is in it (records [0, n_smem)), else through the read-only data cache.
+template <bool kSmem>
+__device__ __forceinline__ int32_t load_slot(const Tree& T, int32_t n_smem, int32_t rec, int k) {
+    if (kSmem && rec < n_smem) return s_nodes[rec * 8 + k];
     return __ldg(T.nodes + (int64_t)rec * 8 + k);
 }
 __device__ __forceinline__ uint2 load_leaf(const Tree& T, int32_t slot) { return __ldg(T.leaves + (-(int64_t)slot - 1)); }
@@ -119,8 +122,6 @@ struct Cold {
 
 struct Ray {
     Cold* k;
-    const int32_t* s_nodes;  // shared-memory copy of the first n_smem records
-    int32_t n_smem;
     float ih[3], il[3];         // inv_d as two FP32 words (0 for d = 0)
     float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
     float sf, sf_eps;           // frame size, frame size * 2^-43
@@ -237,6 +238,7 @@ __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a
 }
 
 // Start ray g of the launch. Returns true if it has a leaf to step from.
+template <bool kSmem>
 __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsigned long long g, int32_t* stk) {
     const Tree& T = P.tree;
     g += (unsigned long long)P.ray_base;
@@ -336,7 +338,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
             r.c[a] = 2u * r.c[a] + b;
             k |= (int)b << a;
         }
-        slot = load_slot(T, r.s_nodes, r.n_smem, rec, k);
+        slot = load_slot<kSmem>(T, P.smem_records, rec, k);
         r.n_rec += 1;
         if (slot > 0) {
             ++lev;
@@ -363,6 +365,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
 }
 
 // One leaf step. Returns false once the ray is finished (its pixel written).
+template <bool kSmem>
 __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_t* stk) {
     const Tree& T = P.tree;
     // 1. exit of the current leaf: double-float crossing times in the frame
@@ -477,7 +480,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             }
             ++Lc;
         }
-        slot = load_slot(T, r.s_nodes, r.n_smem, rec, k);
+        slot = load_slot<kSmem>(T, P.smem_records, rec, k);
         r.n_rec += 1;
         if (slot > 0) {
             ++lev;
@@ -540,16 +543,16 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
+template <bool kSmem>
 __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
     __shared__ Cold cold[kBlock];
-    extern __shared__ int32_t s_nodes[];
-    for (int i = threadIdx.x; i < P.smem_records * 8; i += blockDim.x) s_nodes[i] = __ldg(P.tree.nodes + i);
-    __syncthreads();
+    if (kSmem) {
+        for (int i = threadIdx.x; i < P.smem_records * 8; i += blockDim.x) s_nodes[i] = __ldg(P.tree.nodes + i);
+        __syncthreads();
+    }
     int32_t stk[kMaxDepth + 1];
     Ray r;
     r.k = &cold[threadIdx.x];
-    r.s_nodes = s_nodes;
-    r.n_smem = P.smem_records;
     r.k->n_rays = r.k->n_steps = r.k->n_f64 = r.k->n_rebase = 0;
     r.n_reads = r.n_leaf = r.n_rec = 0;
     const double inv_extent = 1.0 / P.tree.extent;
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
             if (base + __popc(idle) >= (unsigned long long)P.total_rays) drained = true;
             if (!alive) {
                 const unsigned long long g = base + __popc(idle & ((1u << lane) - 1u));
-                if (g < (unsigned long long)P.total_rays) alive = ray_init(r, P, inv_extent, g, stk);
+                if (g < (unsigned long long)P.total_rays) alive = ray_init<kSmem>(r, P, inv_extent, g, stk);
             }
             busy = __ballot_sync(kFull, alive);
             if (!drained && __popc(busy) <= P.refill) continue;
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
             continue;
         }
         do {
-            if (alive) alive = ray_step(r, P, inv_extent, stk);
+            if (alive) alive = ray_step<kSmem>(r, P, inv_extent, stk);
             busy = __ballot_sync(kFull, alive);
         } while (busy != 0u && (drained || __popc(busy) > P.refill));
     }
@@ -591,21 +594,26 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
 }  // namespace
 
 cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s) {
+    if (p.smem_records <= 0) {
+        mixed_kernel<false><<<grid, block, 0, s>>>(p);
+        return cudaGetLastError();
+    }
     const int smem = p.smem_records * 32;
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    mixed_kernel<<<grid, block, smem, s>>>(p);
+    mixed_kernel<true><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out) {
+    if (smem_bytes <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<false>, block, 0);
     if (smem_bytes > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel, block, smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<true>, block, smem_bytes);
 }
 
 }  // namespace canvox
