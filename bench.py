@@ -161,6 +161,22 @@ def oracle_rate(canvas, cams, budget_s, seed=12345):
     return px, ref, done / wall / 1e6, wall, oracle.max_threads()
 
 
+def aggregate_ranks(ms_step, rays, world, device=None):
+    """Whole-job throughput: the slowest rank's time per step, all ranks' rays (replicas, weak scaling).
+    Returns (max ms per step over ranks, Mrays/s of the job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_step), float(rays)], dtype=torch.float64, device=device)
+    if world > 1:
+        m = t[0:1].clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        n = t[1:2].clone()
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        t = torch.cat([m, n])
+    ms_max, total_rays = float(t[0].item()), float(t[1].item())
+    return ms_max, total_rays / (ms_max * 1e-3) / 1e6
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -254,12 +270,8 @@ def main():
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = sum(ms) / len(ms)
     stats = cx.get_stats(check=False)
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     rays = stats["rays"]
-    value = world * rays / (ms_max * 1e-3) / 1e6
+    ms_max, value = aggregate_ranks(ms_step, rays, world, dev)
 
     line = None
     if rank == 0:
@@ -279,7 +291,8 @@ def main():
                        "parallelism": f"replicas x{world}", "opts": cx.default_opts() | opts},
             "stereo_fps": (world / (ms_max * 1e-3)) if len(cams) == 2 else None,
             "wall_ms_per_step_incl_flush": wall * 1e3 / args.steps,
-            "gpu_launches": args.steps * (1 if not opts.get("per_view") else len(cams)),
+            # per render: the eye-path kernel and the traversal kernel (one per view in per-view mode)
+            "gpu_launches": args.steps * (1 + (1 if not opts.get("per_view") else len(cams))),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": algo_bytes,
