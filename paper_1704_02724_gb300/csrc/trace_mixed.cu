@@ -45,7 +45,7 @@ constexpr int kMaxFrameBits = 22;                   // a frame spans at most 22 
 
 // Resident 256-thread blocks per SM the register allocation must allow (occupancy knob).
 #ifndef CANVOX_MIN_BLOCKS
-#define CANVOX_MIN_BLOCKS 3
+#define CANVOX_MIN_BLOCKS 4
 #endif
 
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
@@ -111,13 +111,16 @@ __device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl)
 
 constexpr int kBlock = 256;
 
-// FP64 state and rare counters of a lane: read only by rebases, near-ties and
-// start-up, so it lives in shared memory instead of registers.
+// FP64 state, output address and rare counters of a lane: read only by rebases,
+// near-ties, start-up and the final write, so it lives in shared memory.
 struct Cold {
     double inv64[3], nod64[3];  // t(P) = P inv + nod; axis with d = 0: inv = 0, nod = o
     double tf;                  // FP64 ray parameter at the frame origin
     double invS;                // 1 / frame size
+    int64_t pix;                // output pixel
+    int32_t view;
     uint32_t n_rays, n_steps, n_f64, n_rebase;
+    uint32_t pad;
 };
 
 struct Ray {
@@ -126,21 +129,19 @@ struct Ray {
     float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
     float sf, sf_eps;           // frame size, frame size * 2^-43
     float cur_hi, cur_lo;       // frame-local parameter of the current leaf's entry
-    float C0, C1, C2, k0, k1, k2;
-    float tau, ktau, T;
-    float err;
+    float* acc;  // shared, stride kBlock: C0, C1, C2 (colour), k0, k1, k2 (their Kahan terms), tau, ktau, err
+    float T;
     uint32_t c[3];
     int32_t L, f;
     uint32_t dpos, zmask;
     uint2 val;
     int32_t steps;
-    int32_t view;
-    int64_t pix;
     // counters, summed over every ray the lane traces
     uint32_t n_reads, n_leaf, n_rec;
 };
 
 __device__ __forceinline__ bool is_zero(const Ray& r, int a) { return (r.zmask >> a) & 1u; }
+#define ACC(r, i) ((r).acc[(i) * kBlock])
 
 // Ray on the high side of the global plane x_a = M just after parameter t (FP64).
 __device__ __forceinline__ uint32_t high64(const Ray& r, int a, double M, double t) {
@@ -192,23 +193,23 @@ __device__ __forceinline__ void composite(Ray& r, float teh, float tel) {
         const float x = s * ell;
         const float a = -expm1f(-x);
         const float w = r.T * a;
-        kahan_add(r.C0, r.k0, w * hlo(r.val.x));
-        kahan_add(r.C1, r.k1, w * hhi(r.val.x));
-        kahan_add(r.C2, r.k2, w * hlo(r.val.y));
-        kahan_add(r.tau, r.ktau, x);
-        r.T = expf(-r.tau);
+        kahan_add(ACC(r, 0), ACC(r, 3), w * hlo(r.val.x));
+        kahan_add(ACC(r, 1), ACC(r, 4), w * hhi(r.val.x));
+        kahan_add(ACC(r, 2), ACC(r, 5), w * hlo(r.val.y));
+        kahan_add(ACC(r, 6), ACC(r, 7), x);
+        r.T = expf(-ACC(r, 6));
     }
 }
 
 __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
-    const View& V = P.views[r.view];
+    const View& V = P.views[r.k->view];
     float4 o;
-    o.x = r.C0 + r.T * V.bg[0];
-    o.y = r.C1 + r.T * V.bg[1];
-    o.z = r.C2 + r.T * V.bg[2];
+    o.x = ACC(r, 0) + r.T * V.bg[0];
+    o.y = ACC(r, 1) + r.T * V.bg[1];
+    o.z = ACC(r, 2) + r.T * V.bg[2];
     o.w = 1.0f - r.T;
-    P.out[r.pix] = o;
-    if (P.step_count) P.step_count[r.pix] = r.steps;
+    P.out[r.k->pix] = o;
+    if (P.step_count) P.step_count[r.k->pix] = r.steps;
     r.k->n_rays += 1;
     r.k->n_steps += (uint32_t)r.steps;
 }
@@ -257,12 +258,12 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     const int i = ((int)(tile - ty * (unsigned)V.tiles_x) << wl) + (lane & ((1 << wl) - 1));
     const int j = (int)ty * (32 >> wl) + (lane >> wl);
     if (i >= V.width || j >= V.height) return false;  // padding lane of a ragged tile
-    r.view = lo;
-    r.pix = V.out_offset + (int64_t)j * V.width + i;
-    r.C0 = r.C1 = r.C2 = r.k0 = r.k1 = r.k2 = 0.0f;
-    r.tau = r.ktau = 0.0f;
+    r.k->view = lo;
+    r.k->pix = V.out_offset + (int64_t)j * V.width + i;
+    ACC(r, 0) = ACC(r, 1) = ACC(r, 2) = ACC(r, 3) = ACC(r, 4) = ACC(r, 5) = 0.0f;
+    ACC(r, 6) = ACC(r, 7) = 0.0f;
     r.T = 1.0f;
-    r.err = 0.0f;
+    ACC(r, 8) = 0.0f;
     r.steps = 0;
     // pixel-centre ray in FP64 (Sec. 6.1)
     double d[3];
@@ -298,7 +299,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         finish(r, P);
         return false;
     }
-    const EyePath& E = P.eye[r.view];
+    const EyePath& E = P.eye[r.k->view];
     if (E.len > 0 && t0 == 0.0) {
         // the eye's leaf, located once for the view
         r.L = E.len;
@@ -439,8 +440,8 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         // leaving the canvas: last segment, bounded like a boundary to sigma = 0
         if (!have64 && (r.val.y >> 16)) {
             const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(inv_ax);
-            if (r.err + need > P.err_budget) need64();
-            else r.err += need;
+            if (ACC(r, 8) + need > P.err_budget) need64();
+            else ACC(r, 8) += need;
         }
         composite(r, teh, tel);
         finish(r, P);
@@ -504,8 +505,8 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             need64();
         } else if (nval.x != r.val.x || nval.y != r.val.y) {
             const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(inv_ax);
-            if (r.err + need > P.err_budget) need64();
-            else r.err += need;
+            if (ACC(r, 8) + need > P.err_budget) need64();
+            else ACC(r, 8) += need;
         }
     }
     // 5. composite the current leaf, then terminate or advance
@@ -546,6 +547,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 template <bool kSmem>
 __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
     __shared__ Cold cold[kBlock];
+    __shared__ float accs[9 * kBlock];
     if (kSmem) {
         for (int i = threadIdx.x; i < P.smem_records * 8; i += blockDim.x) s_nodes[i] = __ldg(P.tree.nodes + i);
         __syncthreads();
@@ -553,6 +555,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
     int32_t stk[kMaxDepth + 1];
     Ray r;
     r.k = &cold[threadIdx.x];
+    r.acc = &accs[threadIdx.x];
     r.k->n_rays = r.k->n_steps = r.k->n_f64 = r.k->n_rebase = 0;
     r.n_reads = r.n_leaf = r.n_rec = 0;
     const double inv_extent = 1.0 / P.tree.extent;
