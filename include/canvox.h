@@ -87,6 +87,8 @@ typedef struct canvox_camera {
  *                   memory at kernel start (0 = none, at most 6144; blocks per SM shrink to fit).
  *   frame_levels  : K, the most levels a local frame may sit above its cell (1..22).
  *   tile_w        : pixel tile a warp starts with: tile_w x (32 / tile_w), tile_w in {4, 8, 16, 32}.
+ *   traversal     : 0 = neighbour links (the paper's neighbour graph, Sec. 4.1.1, built at upload),
+ *                   1 = stack of ancestor records with re-descent from the common ancestor.
  *   step_limit    : most leaves one ray may visit (0 = 3 * 2^depth + 8, capped at 2^31 - 1).
  *   t_min         : stop a ray once its transmittance is below this (< 0: default 2^-20).
  *   err_budget    : per-ray bound on the colour error the FP32 boundaries may add before
@@ -103,6 +105,7 @@ typedef struct canvox_render_opts {
     int32_t smem_records;
     int32_t frame_levels;
     int32_t tile_w;
+    int32_t traversal;
     int64_t step_limit;
     float t_min;
     float err_budget;
@@ -138,7 +141,8 @@ void canvox_default_opts(canvox_render_opts* o);
  *   depth      : deepest level allowed (1..30); the finest cell is extent * 2^-depth.
  *   extent     : canvas side (> 0, finite, at most 23 significant bits so that
  *                every cell plane is exact in FP64).
- * Validation (CANVOX_ERR_BAD_TREE on failure, previous canvas kept): internal
+ * The upload also builds six neighbour links per record (48 bytes per record) for the
+ * default traversal. Validation (CANVOX_ERR_BAD_TREE on failure, previous canvas kept): internal
  * children numbered 1, 2, ... in breadth-first order (each referenced once,
  * no cycles), leaves numbered 0, 1, ... in the same order, no record deeper
  * than depth - 1, leaf values finite with sigma >= 0. The host pools may be

@@ -48,6 +48,7 @@ class Opts(ctypes.Structure):
         ("smem_records", ctypes.c_int32),
         ("frame_levels", ctypes.c_int32),
         ("tile_w", ctypes.c_int32),
+        ("traversal", ctypes.c_int32),
         ("step_limit", ctypes.c_int64),
         ("t_min", ctypes.c_float),
         ("err_budget", ctypes.c_float),

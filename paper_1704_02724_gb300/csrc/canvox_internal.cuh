@@ -17,6 +17,7 @@ constexpr int kMaxSmemRecords = 6144;
 // Device view of the uploaded canvas.
 struct Tree {
     const int32_t* nodes;  // n_rec x 8 child slots
+    const uint2* ropes;    // n_rec x 6 face neighbours (null: none built), see rope_level_kernel
     const uint2* leaves;   // n_leaf x FP16 (R,G | B,sigma)
     int64_t n_rec;
     int64_t n_leaf;
@@ -92,6 +93,7 @@ struct MixedParams {
     float err_budget;
     int32_t frame_levels;
     int32_t smem_records;
+    int32_t use_ropes;   // 1: neighbour links (Tree::ropes), 0: stack of ancestors
 };
 
 struct PlainParams {
@@ -109,6 +111,7 @@ cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out);
 cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, int64_t hi, int level, cudaStream_t s);
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 
 // Host helpers of runtime.cu shared with other entry points.

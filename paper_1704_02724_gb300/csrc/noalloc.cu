@@ -91,6 +91,7 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
     if (e == cudaSuccess) e = cudaMemcpyAsync(views, hv, sizeof(View) * (size_t)n_views, cudaMemcpyHostToDevice, s);
     Tree t;
     t.nodes = node_pool_dev;
+    t.ropes = nullptr;
     t.leaves = reinterpret_cast<const uint2*>(leaf_rgba_dev);
     t.n_rec = n_records;
     t.n_leaf = n_leaves;
@@ -119,6 +120,7 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
     p.err_budget = o.err_budget;
     p.frame_levels = o.frame_levels;
     p.smem_records = 0;
+    p.use_ropes = 0;  // no neighbour links without allocating them
     e = launch_mixed(p, sms * (bps > 0 ? bps : 1), o.block_threads, s);
     if (e != cudaSuccess) return set_error(CANVOX_ERR_CUDA, cudaGetErrorString(e));
     return CANVOX_OK;

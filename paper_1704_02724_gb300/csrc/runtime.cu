@@ -59,6 +59,7 @@ struct Ctx {
     // canvas
     int32_t* d_nodes = nullptr;
     uint2* d_leaves = nullptr;
+    uint2* d_ropes = nullptr;
     int64_t n_rec = 0, n_leaf = 0;
     int32_t depth = 0;
     double extent = 0.0;
@@ -103,6 +104,7 @@ void builtin_defaults(canvox_render_opts* o) {
     o->smem_records = 0;
     o->frame_levels = 20;
     o->tile_w = 8;
+    o->traversal = 0;
     o->step_limit = 0;
     o->t_min = -1.0f;
     o->err_budget = 3.0e-6f;
@@ -235,6 +237,7 @@ int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (o->tile_w == 0) o->tile_w = 8;
     if (o->tile_w != 4 && o->tile_w != 8 && o->tile_w != 16 && o->tile_w != 32)
         return fail(CANVOX_ERR_INVALID_ARG, "tile_w %d (4, 8, 16 or 32)", o->tile_w);
+    if (o->traversal != 0 && o->traversal != 1) return fail(CANVOX_ERR_INVALID_ARG, "traversal %d (0 or 1)", o->traversal);
     if (!(o->err_budget >= 0.0f) || !std::isfinite(o->err_budget)) return fail(CANVOX_ERR_INVALID_ARG, "err_budget");
     if (!std::isfinite(o->t_min)) return fail(CANVOX_ERR_INVALID_ARG, "t_min");
     if (o->t_min < 0.0f) o->t_min = 9.5367431640625e-07f;  // 2^-20
@@ -253,6 +256,7 @@ int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
 Tree device_tree() {
     Tree t;
     t.nodes = g.d_nodes;
+    t.ropes = g.d_ropes;
     t.leaves = g.d_leaves;
     t.n_rec = g.n_rec;
     t.n_leaf = g.n_leaf;
@@ -284,6 +288,7 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
         p.frame_levels = o.frame_levels;
         p.refill = o.refill;
         p.smem_records = o.smem_records;
+        p.use_ropes = o.traversal == 0 ? 1 : 0;
         if (!o.per_view) {
             p.views = g.d_views;
             p.eye = g.d_eye;
@@ -410,8 +415,10 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     drop_graphs();
     if (g.d_nodes) cudaFree(g.d_nodes);
     if (g.d_leaves) cudaFree(g.d_leaves);
+    if (g.d_ropes) cudaFree(g.d_ropes);
     g.d_nodes = nullptr;
     g.d_leaves = nullptr;
+    g.d_ropes = nullptr;
     g.uploaded = false;
     CK(cudaMalloc(&g.d_nodes, sizeof(int32_t) * 8 * (size_t)n_records), "cudaMalloc(nodes)");
     CK(cudaMalloc(&g.d_leaves, sizeof(uint2) * (size_t)(n_leaves > 0 ? n_leaves : 1)), "cudaMalloc(leaves)");
@@ -429,6 +436,19 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     unsigned long long dh = 0;
     CK(cudaMemcpy(&dh, g.d_hash, sizeof(dh), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
     if (dh != hh) return fail(CANVOX_ERR_CUDA, "device copy hash %016llx differs from host %016llx", dh, hh);
+    // neighbour links, level by level (breadth-first order keeps each level contiguous)
+    CK(cudaMalloc(&g.d_ropes, sizeof(uint2) * 6 * (size_t)n_records), "cudaMalloc(ropes)");
+    {
+        int64_t lo = 0;
+        while (lo < n_records) {
+            int64_t hi = lo;
+            const int lev = level[(size_t)lo];
+            while (hi < n_records && level[(size_t)hi] == lev) ++hi;
+            CK(launch_rope_level(g.d_nodes, g.d_ropes, lo, hi, lev, 0), "rope kernel launch");
+            lo = hi;
+        }
+        CK(cudaDeviceSynchronize(), "rope build");
+    }
     g.uploaded = true;
     return CANVOX_OK;
 }
@@ -659,6 +679,7 @@ void canvox_release(void) {
     drop_graphs();
     if (g.d_nodes) cudaFree(g.d_nodes);
     if (g.d_leaves) cudaFree(g.d_leaves);
+    if (g.d_ropes) cudaFree(g.d_ropes);
     if (g.d_views) cudaFree(g.d_views);
     if (g.d_eye) cudaFree(g.d_eye);
     for (int b = 0; b < 2; ++b) {

@@ -135,6 +135,8 @@ struct Ray {
     int32_t L, f;
     uint32_t dpos, zmask;
     uint2 val;
+    int32_t pr;   // record holding the current leaf's slot (neighbour-link traversal)
+    uint32_t kc;  // child index of the current leaf in pr
     int32_t steps;
     // counters, summed over every ray the lane traces
     uint32_t n_reads, n_leaf, n_rec;
@@ -239,7 +241,7 @@ __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a
 }
 
 // Start ray g of the launch. Returns true if it has a leaf to step from.
-template <bool kSmem>
+template <bool kSmem, bool kRopes>
 __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsigned long long g, int32_t* stk) {
     const Tree& T = P.tree;
     g += (unsigned long long)P.ray_base;
@@ -303,7 +305,12 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     if (E.len > 0 && t0 == 0.0) {
         // the eye's leaf, located once for the view
         r.L = E.len;
-        for (int l = 0; l < E.len; ++l) stk[l] = E.rec[l];
+        if (kRopes) {
+            r.pr = E.rec[E.len - 1];
+            r.kc = (E.c[0] & 1u) | ((E.c[1] & 1u) << 1) | ((E.c[2] & 1u) << 2);
+        } else {
+            for (int l = 0; l < E.len; ++l) stk[l] = E.rec[l];
+        }
         r.c[0] = E.c[0];
         r.c[1] = E.c[1];
         r.c[2] = E.c[2];
@@ -343,9 +350,11 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         r.n_rec += 1;
         if (slot > 0) {
             ++lev;
-            stk[lev] = slot;
+            if (!kRopes) stk[lev] = slot;
             rec = slot;
         } else {
+            r.pr = rec;
+            r.kc = (uint32_t)k;
             break;
         }
     }
@@ -366,7 +375,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
 }
 
 // One leaf step. Returns false once the ray is finished (its pixel written).
-template <bool kSmem>
+template <bool kSmem, bool kRopes>
 __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_t* stk) {
     const Tree& T = P.tree;
     // 1. exit of the current leaf: double-float crossing times in the frame
@@ -450,17 +459,40 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     const int lstar = r.L - (32 - __clz(cold ^ cn));
     const bool fexit = lstar < r.f;
     if (fexit) need64();
-    // 3. re-descend from the common ancestor
+    // 3. the new leaf: start at the neighbouring cell (a sibling, the parent's neighbour link,
+    //    or the common ancestor on the stack), then descend while the cell is internal
     uint32_t cc[3] = {ax == 0 ? cn : r.c[0], ax == 1 ? cn : r.c[1], ax == 2 ? cn : r.c[2]};
     int Lc = r.L;
-    int lev = lstar;
-    int32_t rec = stk[lstar];
-    int32_t slot;
+    int lv;         // level of the cell in slot (prec, kk)
+    int32_t prec;
+    int kk;
+    if (kRopes) {
+        if (lstar == r.L - 1) {
+            prec = r.pr;
+            kk = (int)(r.kc ^ (1u << ax));
+            lv = r.L;
+        } else {
+            const uint2 rp = __ldg(T.ropes + (int64_t)r.pr * 6 + 2 * ax + (int)up);
+            r.n_rec += 1;
+            prec = (int32_t)rp.x;
+            kk = (int)((rp.y >> 8) & 7u);
+            lv = (int)(rp.y & 255u);
+        }
+    } else {
+        prec = stk[lstar];
+        lv = lstar + 1;
+        const int sh = Lc - lv;
+        kk = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
+    }
+    int32_t slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
+    r.n_rec += 1;
     const float margin_ax = kEpsDF * fabsf(inv_ax);
-    for (;;) {
+    while (slot > 0) {
+        // internal cell at level lv (record `slot`): choose its child at level lv + 1
+        if (!kRopes) stk[lv] = slot;
         int k;
-        if (lev < Lc) {
-            const int sh = Lc - 1 - lev;
+        if (lv < Lc) {
+            const int sh = Lc - 1 - lv;
             k = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
         } else {
             // finer than the old cell: near side on the exit axis, ray position on the others
@@ -471,26 +503,23 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
                 if (a == ax) {
                     bit = up ? 0u : 1u;
                 } else if (fexit) {
-                    const double M = fma((double)(2u * cc[a] + 1u), T.extent * pow2d(-(lev + 1)), -T.half);
+                    const double M = fma((double)(2u * cc[a] + 1u), T.extent * pow2d(-(lv + 1)), -T.half);
                     bit = high64(r, a, M, te64);
                 } else {
-                    bit = child_bit(r, T, a, cc[a], lev, teh, tel, margin_ax, need64);
+                    bit = child_bit(r, T, a, cc[a], lv, teh, tel, margin_ax, need64);
                 }
                 cc[a] = 2u * cc[a] + bit;
                 k |= (int)bit << a;
             }
             ++Lc;
         }
-        slot = load_slot<kSmem>(T, P.smem_records, rec, k);
+        prec = slot;
+        kk = k;
+        ++lv;
+        slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
         r.n_rec += 1;
-        if (slot > 0) {
-            ++lev;
-            stk[lev] = slot;
-            rec = slot;
-        } else {
-            break;
-        }
     }
+    const int lev = lv - 1;
     const int Ln = lev + 1;
     r.n_reads += (uint32_t)(Ln - lstar);
     uint2 nval = make_uint2(0u, 0u);
@@ -527,6 +556,10 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     r.c[2] = cc[2] >> sh;
     r.L = Ln;
     r.val = nval;
+    if (kRopes) {
+        r.pr = prec;
+        r.kc = (uint32_t)kk;
+    }
     r.steps += 1;
     if (rebase) {
         r.f = max(0, Ln - P.frame_levels);
@@ -544,7 +577,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-template <bool kSmem>
+template <bool kSmem, bool kRopes>
 __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
     __shared__ Cold cold[kBlock];
     __shared__ float accs[9 * kBlock];
@@ -552,7 +585,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
         for (int i = threadIdx.x; i < P.smem_records * 8; i += blockDim.x) s_nodes[i] = __ldg(P.tree.nodes + i);
         __syncthreads();
     }
-    int32_t stk[kMaxDepth + 1];
+    int32_t stk[kRopes ? 1 : kMaxDepth + 1];  // ancestors by level (stack traversal only)
     Ray r;
     r.k = &cold[threadIdx.x];
     r.acc = &accs[threadIdx.x];
@@ -572,7 +605,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
             if (base + __popc(idle) >= (unsigned long long)P.total_rays) drained = true;
             if (!alive) {
                 const unsigned long long g = base + __popc(idle & ((1u << lane) - 1u));
-                if (g < (unsigned long long)P.total_rays) alive = ray_init<kSmem>(r, P, inv_extent, g, stk);
+                if (g < (unsigned long long)P.total_rays) alive = ray_init<kSmem, kRopes>(r, P, inv_extent, g, stk);
             }
             busy = __ballot_sync(kFull, alive);
             if (!drained && __popc(busy) <= P.refill) continue;
@@ -582,7 +615,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
             continue;
         }
         do {
-            if (alive) alive = ray_step<kSmem>(r, P, inv_extent, stk);
+            if (alive) alive = ray_step<kSmem, kRopes>(r, P, inv_extent, stk);
             busy = __ballot_sync(kFull, alive);
         } while (busy != 0u && (drained || __popc(busy) > P.refill));
     }
@@ -596,27 +629,36 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
 
 }  // namespace
 
-cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s) {
+template <bool kRopes>
+cudaError_t launch_mixed_t(const MixedParams& p, int grid, int block, cudaStream_t s) {
     if (p.smem_records <= 0) {
-        mixed_kernel<false><<<grid, block, 0, s>>>(p);
+        mixed_kernel<false, kRopes><<<grid, block, 0, s>>>(p);
         return cudaGetLastError();
     }
     const int smem = p.smem_records * 32;
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const cudaError_t e =
+            cudaFuncSetAttribute(mixed_kernel<true, kRopes>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    mixed_kernel<true><<<grid, block, smem, s>>>(p);
+    mixed_kernel<true, kRopes><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
+cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s) {
+    return (p.use_ropes && p.tree.ropes) ? launch_mixed_t<true>(p, grid, block, s) : launch_mixed_t<false>(p, grid, block, s);
+}
+
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out) {
-    if (smem_bytes <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<false>, block, 0);
+    // all four instances share the register and static shared-memory budget
+    if (smem_bytes <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<false, true>, block, 0);
     if (smem_bytes > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mixed_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<true>, block, smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<true, true>, block, smem_bytes);
 }
 
 }  // namespace canvox

@@ -224,7 +224,50 @@ __global__ void eye_path_kernel(Tree t, const View* views, int n_views, EyePath*
     }
 }
 
+// Neighbour links (the paper's neighbour graph of Sec. 4.1.1, kept per record).
+// ropes[r][2a + s] names the cell across face (axis a, s = 1 high / 0 low) of
+// record r's cell: the same-level neighbour if it exists, else the coarser leaf
+// that covers it, as (record holding its slot, (child index << 8) | its level);
+// record -1 is outside the canvas. One launch per level, parents before
+// children: a child's link is its sibling inside the parent, or the parent's
+// link, refined to the adjacent child when that neighbour is an internal cell.
+__global__ void rope_level_kernel(const int32_t* nodes, uint2* ropes, long long lo, long long hi, int level) {
+    const long long r = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= hi) return;
+    if (level == 0) {
+        for (int f = 0; f < 6; ++f) ropes[r * 6 + f] = make_uint2(0xFFFFFFFFu, 0u);
+    }
+    for (int k = 0; k < 8; ++k) {
+        const int32_t v = nodes[r * 8 + k];
+        if (v <= 0) continue;
+        for (int f = 0; f < 6; ++f) {
+            const int a = f >> 1, hi_face = f & 1;
+            const int bit = (k >> a) & 1;
+            const unsigned kk = (unsigned)(k ^ (1 << a));
+            uint2 out;
+            if (hi_face != bit) {
+                out = make_uint2((unsigned)r, (kk << 8) | (unsigned)(level + 1));  // sibling inside r
+            } else {
+                const uint2 R = ropes[r * 6 + f];
+                out = R;
+                if ((int)R.x >= 0) {
+                    const int32_t sv = nodes[(long long)(int)R.x * 8 + ((R.y >> 8) & 7u)];
+                    if (sv > 0) out = make_uint2((unsigned)sv, (kk << 8) | (unsigned)(level + 1));
+                }
+            }
+            ropes[(long long)v * 6 + f] = out;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, int64_t hi, int level, cudaStream_t s) {
+    if (hi <= lo) return cudaSuccess;
+    const long long n = hi - lo;
+    rope_level_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nodes, ropes, lo, hi, level);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s) {
     if (n_views <= 0) return cudaSuccess;
