@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 baseline, e2e and CPU baseline")
     ap.add_argument("--opts", type=str, default="", help="render options as JSON")
+    ap.add_argument("--no-autotune", action="store_true", help="time the built-in default schedule")
     ap.add_argument("--res-scale", type=float, default=1.0, help="shrink every image side (profiling cases)")
     ap.add_argument("--n-fine", type=int, default=0, help="fine stamps of configs 2-4 (profiling cases; 0 = config)")
     return ap.parse_args()
@@ -249,6 +250,13 @@ def main():
     out = torch.empty((n_px, 4), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_autotune and not opts:
+        # the schedule (tile shape, refill, shared-memory prefix, frame depth, traversal) picked by
+        # the library's autotuner on these views; it becomes the default for the renders below
+        t_tune = time.perf_counter()
+        tuned = cx.autotune(cams)
+        tuned["seconds"] = round(time.perf_counter() - t_tune, 1)
     for _ in range(max(3, args.warmup)):
         cx.render(cams, out, **opts)
     torch.cuda.synchronize()
@@ -288,7 +296,8 @@ def main():
                        + f" ({len(cams)} views, {n_px} rays, depth {canvas.depth},"
                        f" {canvas.n_records} records, {canvas.n_leaves} leaves)",
                        "rays_per_step": rays * world, "l2": "flushed before every timed step (256 MB write)",
-                       "parallelism": f"replicas x{world}", "opts": cx.default_opts() | opts},
+                       "parallelism": f"replicas x{world}", "opts": cx.default_opts() | opts,
+                       "schedule": "autotuned" if tuned else ("given" if opts else "built-in default")},
             "stereo_fps": (world / (ms_max * 1e-3)) if len(cams) == 2 else None,
             "wall_ms_per_step_incl_flush": wall * 1e3 / args.steps,
             # per render: the eye-path kernel and the traversal kernel (one per view in per-view mode)
@@ -301,6 +310,7 @@ def main():
                          "bytes_formula": "32*slot_reads + 8*leaf_loads + 16*rays"},
             "stats": {k: v for k, v in stats.items() if k != "status"},
             "hash_ok": h_hash == d_hash,
+            "autotune": tuned,
             "clocks": clk,
         }
     if rank == 0 and not args.no_extras and world == 1:

@@ -206,7 +206,7 @@ int canvox_octree_hash(uint64_t* host_hash, uint64_t* device_hash);
 
 /*
  * Search the schedule (block size, refill threshold, tile shape, shared-memory
- * prefix, frame levels; one parameter at a time, two passes) by timing renders
+ * prefix, frame levels, traversal; one parameter at a time, two passes) by timing renders
  * of these views, and keep the fastest as the default options. Synchronous. Writes the chosen options to *best when
  * best is not NULL.
  */

@@ -643,14 +643,16 @@ int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, ca
     const int tiles[] = {4, 8, 16, 32};
     const int smems[] = {0, 256, 1024, 4096};
     const int frames[] = {16, 20, 22};
+    const int traversals[] = {0, 1};
     for (int pass = 0; pass < 2 && rc == CANVOX_OK; ++pass) {
-        for (int which = 0; which < 5 && rc == CANVOX_OK; ++which) {
-            const int* vals = which == 0 ? blocks : which == 1 ? refills : which == 2 ? tiles : which == 3 ? smems : frames;
-            const int nv = which == 0 ? 2 : which == 1 ? 3 : which == 2 ? 4 : which == 3 ? 4 : 3;
+        for (int which = 0; which < 6 && rc == CANVOX_OK; ++which) {
+            const int* vals = which == 0 ? blocks : which == 1 ? refills : which == 2 ? tiles : which == 3 ? smems
+                            : which == 4 ? frames : traversals;
+            const int nv = which == 0 ? 2 : which == 1 ? 3 : which == 2 ? 4 : which == 3 ? 4 : which == 4 ? 3 : 2;
             for (int i = 0; i < nv && rc == CANVOX_OK; ++i) {
                 canvox_render_opts o = win;
                 int* field = which == 0 ? &o.block_threads : which == 1 ? &o.refill : which == 2 ? &o.tile_w
-                             : which == 3 ? &o.smem_records : &o.frame_levels;
+                             : which == 3 ? &o.smem_records : which == 4 ? &o.frame_levels : &o.traversal;
                 if (*field == vals[i]) continue;
                 *field = vals[i];
                 o.blocks_per_sm = 0;
