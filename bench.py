@@ -344,6 +344,20 @@ def main():
         st2 = cx.get_stats(check=False)
         line["e2e"] = {"value": rays / e2e_s / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": st2["h2d_bytes"],
                        "d2h_bytes_per_step": st2["d2h_bytes"], "ms_per_step": e2e_s * 1e3}
+        # the paper's FP32 walks (Sec. 6.3): cell-local and canvas-coordinate, with ray-angle errors
+        walks = {}
+        for name, prec in (("cell32", cx.PREC_CELL32), ("world32", cx.PREC_WORLD32)):
+            img_w = torch.empty_like(out)
+            ang = torch.zeros(n_px, dtype=torch.float32, device=dev)
+            e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0_.record(stream)
+            cx.render(cams, img_w, precision=prec, angle_deg=ang)
+            e1_.record(stream)
+            torch.cuda.synchronize()
+            a = ang.cpu().numpy().astype(np.float64)
+            walks[name] = {"image": img_w, "ms": e0_.elapsed_time(e1_),
+                           "angle_deg_max": float(a.max()), "angle_deg_p99_9": float(np.percentile(a, 99.9)),
+                           "angle_deg_median": float(np.median(a))}
         # FP64 oracle on host cores: CPU baseline and the error of each GPU path on its sample
         px, ref, rate, wall_s, cores = oracle_rate(canvas, cams, args.cpu_seconds)
         img = out.cpu().numpy().astype(np.float64)[px]
@@ -355,6 +369,10 @@ def main():
             "fp64_plain": float(np.abs(out64.cpu().numpy().astype(np.float64)[px] - ref).max()),
             "fp32_plain": float(np.abs(out32.cpu().numpy().astype(np.float64)[px] - ref).max()),
             "pixels": int(len(px))}
+        for name, w in walks.items():
+            w["max_err_vs_oracle"] = float(np.abs(w.pop("image").cpu().numpy().astype(np.float64)[px] - ref).max())
+            w["Mrays_s"] = rays / (w.pop("ms") * 1e-3) / 1e6
+        line["paper_fp32_walks"] = walks
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

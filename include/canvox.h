@@ -38,6 +38,8 @@ extern "C" {
 #define CANVOX_PREC_MIXED 0 /* FP32 cell-local frames, FP64 rebase and error-budgeted FP64 boundaries */
 #define CANVOX_PREC_FP64 1  /* plain FP64: canvas coordinates, leaf located from the root each step */
 #define CANVOX_PREC_FP32 2  /* plain FP32 in canvas coordinates (the failing baseline of Sec. 6.3) */
+#define CANVOX_PREC_CELL32 3  /* the paper's FP32 cell-local walk, p' s + c per step (Sec. 6.2-6.3) */
+#define CANVOX_PREC_WORLD32 4 /* the same walk with the position in FP32 canvas coordinates (Sec. 6.3 comparison) */
 
 /*
  * One view (Sec. 6.1: the eye position is kept in FP64 canvas coordinates so
@@ -94,6 +96,9 @@ typedef struct canvox_camera {
  *   err_budget    : per-ray bound on the colour error the FP32 boundaries may add before
  *                   the remaining boundaries are taken in FP64 (mixed precision only).
  *   step_count    : optional device int32 per output pixel: leaves visited by its ray.
+ *   angle_deg     : optional device float per output pixel (CELL32 / WORLD32 only): angle in degrees
+ *                   between the initial ray direction and the line from the eye to the ray's final
+ *                   position (the ray-angle error of Sec. 6.3).
  */
 typedef struct canvox_render_opts {
     int32_t precision;
@@ -110,6 +115,7 @@ typedef struct canvox_render_opts {
     float t_min;
     float err_budget;
     int32_t* step_count;
+    float* angle_deg;
 } canvox_render_opts;
 
 /* Counters of the last completed render call (sums over all its rays). */

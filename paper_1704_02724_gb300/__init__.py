@@ -11,6 +11,8 @@ from .canvox import (  # noqa: F401
     PREC_MIXED,
     PREC_FP64,
     PREC_FP32,
+    PREC_CELL32,
+    PREC_WORLD32,
     lib,
     upload_octree,
     render,

@@ -26,6 +26,8 @@ ERR_NAMES = {-1: "INVALID_ARG", -2: "NOT_UPLOADED", -3: "BAD_TREE", -4: "CUDA", 
 PREC_MIXED = 0
 PREC_FP64 = 1
 PREC_FP32 = 2
+PREC_CELL32 = 3
+PREC_WORLD32 = 4
 
 # canvox_camera: 136 bytes (eye, right, up, forward: FP64[3]; tan; width, height; offset; background FP32[4])
 CAMERA_BYTES = 136
@@ -53,6 +55,7 @@ class Opts(ctypes.Structure):
         ("t_min", ctypes.c_float),
         ("err_budget", ctypes.c_float),
         ("step_count", ctypes.c_void_p),
+        ("angle_deg", ctypes.c_void_p),
     ]
 
 
@@ -109,7 +112,7 @@ def _check(rc):
 
 
 def _opts_to_dict(o):
-    return {n: getattr(o, n) for n, _ in Opts._fields_ if n != "step_count"}
+    return {n: getattr(o, n) for n, _ in Opts._fields_ if n not in ("step_count", "angle_deg")}
 
 
 def default_opts():
@@ -122,7 +125,7 @@ def make_opts(**kw):
     o = Opts()
     lib().canvox_default_opts(ctypes.byref(o))
     for k, v in kw.items():
-        if k == "step_count":
+        if k in ("step_count", "angle_deg"):
             v = _dev_ptr(v) if v is not None else None
         elif not hasattr(o, k):
             raise TypeError(f"unknown render option {k!r}")

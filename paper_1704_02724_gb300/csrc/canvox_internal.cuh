@@ -101,6 +101,7 @@ struct PlainParams {
     const View* view;  // one view per launch
     float4* out;
     int32_t* step_count;
+    float* angle_deg;  // per-pixel ray-angle error (single-precision traversals of the paper only)
     Scratch* scratch;
     int64_t step_limit;
     float t_min;
@@ -110,6 +111,7 @@ struct PlainParams {
 cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s);  // smem from p.smem_records
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out);
 cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
+cudaError_t launch_local32(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, int64_t hi, int level, cudaStream_t s);
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);

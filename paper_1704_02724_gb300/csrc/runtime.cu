@@ -109,6 +109,7 @@ void builtin_defaults(canvox_render_opts* o) {
     o->t_min = -1.0f;
     o->err_budget = 3.0e-6f;
     o->step_count = nullptr;
+    o->angle_deg = nullptr;
 }
 
 int ensure_device() {
@@ -223,7 +224,7 @@ int setup_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t
 int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (in) *o = *in;
     else canvox_default_opts(o);
-    if (o->precision < 0 || o->precision > 2) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
+    if (o->precision < 0 || o->precision > 4) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
     if (o->block_threads == 0) o->block_threads = 256;
     if (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)
         return fail(CANVOX_ERR_INVALID_ARG, "block_threads %d (multiple of 32, at most 256)", o->block_threads);
@@ -322,9 +323,14 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
         p.scratch = g.d_scratch;
         p.step_limit = o.step_limit;
         p.t_min = o.t_min;
+        p.angle_deg = o.angle_deg;
         for (int v = 0; v < n; ++v) {
             p.view = g.d_views + v;
-            CK(launch_plain(p, o.precision, (long long)views_host[v].width * views_host[v].height, s), "plain kernel launch");
+            const long long npx = (long long)views_host[v].width * views_host[v].height;
+            if (o.precision == CANVOX_PREC_CELL32 || o.precision == CANVOX_PREC_WORLD32)
+                CK(launch_local32(p, o.precision, npx, s), "single-precision walk launch");
+            else
+                CK(launch_plain(p, o.precision, npx, s), "plain kernel launch");
         }
     }
     return CANVOX_OK;
