@@ -33,9 +33,9 @@ def test_cell_local_walk_shallow_canvas():
     img, ang = _angles(cv, cams, "c0", cx.PREC_CELL32)
     assert np.all(np.isfinite(img)) and np.all(np.isfinite(ang))
     assert max_err(img, ref) <= 1e-3
-    # every ray here starts on the cube (e0 <= sqrt(3) 2^-25 of a depth-8 cell) and travels at least 2 units
+    # every ray starts on the cube, in a cell of side at most 1/2, at least 1.5 units from the eye
     e0 = math.sqrt(3) * 2.0 ** -25 * 2.0 ** -1
-    bound = math.degrees(math.asin(math.sqrt(2) * (e0 / 2.0 + 7.5 * EPS)))
+    bound = math.degrees(math.asin(math.sqrt(2) * (e0 / 1.5 + 7.5 * EPS)))
     assert np.max(ang) <= bound
 
 
