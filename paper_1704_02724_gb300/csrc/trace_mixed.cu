@@ -635,12 +635,10 @@ cudaError_t launch_mixed_t(const MixedParams& p, int grid, int block, cudaStream
         mixed_kernel<false, kRopes><<<grid, block, 0, s>>>(p);
         return cudaGetLastError();
     }
+    // static (per-lane records) plus dynamic shared memory passes the 48 KB default: always opt in
     const int smem = p.smem_records * 32;
-    if (smem > 48 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(mixed_kernel<true, kRopes>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
+    const cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true, kRopes>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     mixed_kernel<true, kRopes><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -652,12 +650,10 @@ cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out) {
     // all four instances share the register and static shared-memory budget
     if (smem_bytes <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<false, true>, block, 0);
-    if (smem_bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mixed_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mixed_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<true, true>, block, smem_bytes);
 }
 

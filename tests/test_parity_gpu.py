@@ -173,7 +173,8 @@ def test_schedules_agree_bitwise():
     base, _ = render(cv, cams, key="c0")
     for kw in (dict(per_view=1), dict(use_graph=1), dict(use_graph=1), dict(refill=0, block_threads=128),
                dict(refill=31, blocks_per_sm=1), dict(tile_w=4), dict(tile_w=32, refill=2), dict(tile_w=16),
-               dict(smem_records=100), dict(smem_records=6144, block_threads=128), dict(traversal=1),
+               dict(smem_records=1024, block_threads=128), dict(smem_records=100),
+               dict(smem_records=6144, block_threads=128), dict(traversal=1),
                dict(traversal=1, smem_records=100), dict(traversal=1, per_view=1)):
         img, _ = render(cv, cams, key="c0", **kw)
         np.testing.assert_array_equal(img, base, err_msg=str(kw))
