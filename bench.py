@@ -136,10 +136,11 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_rate(canvas, cams, budget_s, seed=12345):
-    """Time the FP64 oracle on a seeded pixel sample sized for ~budget_s on all host cores."""
+def oracle_rate(canvas, cams, budget_s, seed=12345, threads=0):
+    """Time the FP64 oracle on a seeded pixel sample sized for ~budget_s (threads 0: all host cores)."""
     import oracle
     import synth
+    threads = threads or oracle.max_threads()
     total = synth.total_pixels(cams)
     rng = np.random.default_rng(seed)
     order = rng.permutation(total).astype(np.int64)
@@ -148,7 +149,7 @@ def oracle_rate(canvas, cams, budget_s, seed=12345):
     while done < total:
         px = order[done:done + n]
         t = time.perf_counter()
-        out.append((px, oracle.render(canvas, cams, px_idx=px)))
+        out.append((px, oracle.render(canvas, cams, px_idx=px, threads=threads, counters=True)))
         dt = time.perf_counter() - t
         spent += dt
         done += len(px)
@@ -158,8 +159,22 @@ def oracle_rate(canvas, cams, budget_s, seed=12345):
         n = int(min(max(256, rate * (budget_s - spent) * 0.5), 1 << 20))
     wall = time.perf_counter() - t_start
     px = np.concatenate([p for p, _ in out])
-    ref = np.concatenate([r for _, r in out])
-    return px, ref, done / wall / 1e6, wall, oracle.max_threads()
+    ref = np.concatenate([r[0] for _, r in out])
+    counts = {"steps": np.concatenate([r[1][:, 0] for _, r in out]),
+              "length": np.concatenate([r[2][:, 1] for _, r in out])}
+    return px, ref, done / wall / 1e6, wall, threads, counts
+
+
+def binned(values, keys, edges):
+    """Median and max of values per [edges[i], edges[i+1]) bin of keys (empty bins left out)."""
+    rows = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        m = (keys >= lo) & (keys < hi)
+        if np.any(m):
+            v = values[m]
+            rows.append({"from": lo, "to": hi, "n": int(m.sum()), "median": float(np.median(v)),
+                         "max": float(v.max())})
+    return rows
 
 
 def aggregate_ranks(ms_step, rays, world, device=None):
@@ -346,7 +361,7 @@ def main():
                        "d2h_bytes_per_step": st2["d2h_bytes"], "ms_per_step": e2e_s * 1e3}
         # the paper's FP32 walks (Sec. 6.3): cell-local and canvas-coordinate, with ray-angle errors
         walks = {}
-        for name, prec in (("cell32", cx.PREC_CELL32), ("world32", cx.PREC_WORLD32)):
+        for name, prec in (("cell32", cx.PREC_CELL32), ("world32", cx.PREC_WORLD32), ("cell16", cx.PREC_CELL16)):
             img_w = torch.empty_like(out)
             ang = torch.zeros(n_px, dtype=torch.float32, device=dev)
             e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -355,11 +370,22 @@ def main():
             e1_.record(stream)
             torch.cuda.synchronize()
             a = ang.cpu().numpy().astype(np.float64)
-            walks[name] = {"image": img_w, "ms": e0_.elapsed_time(e1_),
+            walks[name] = {"image": img_w, "ms": e0_.elapsed_time(e1_), "angles": a,
                            "angle_deg_max": float(a.max()), "angle_deg_p99_9": float(np.percentile(a, 99.9)),
                            "angle_deg_median": float(np.median(a))}
+        # measurement helpers: L2 sector-gather and FP64 probes, the frame's footprint (compulsory bytes)
+        l2_gbs = cx.probe_l2_gather()
+        line["l2_gather"] = {"probe_gbs": l2_gbs, "achieved_gbs": achieved, "frac": achieved / l2_gbs,
+                             "note": "random 32 B sector gathers from a half-L2 buffer, L1 bypassed"}
+        line["fp64_probe_gflops"] = cx.probe_fp64()
+        t_fp = time.perf_counter()
+        n_rec_fp, n_leaf_fp = cx.footprint(cams)
+        line["footprint"] = {"records": n_rec_fp, "leaves": n_leaf_fp,
+                             "compulsory_bytes": 32 * n_rec_fp + 8 * n_leaf_fp,
+                             "with_links_bytes": 80 * n_rec_fp + 8 * n_leaf_fp,
+                             "dram_bytes_per_launch": traffic, "seconds": round(time.perf_counter() - t_fp, 1)}
         # FP64 oracle on host cores: CPU baseline and the error of each GPU path on its sample
-        px, ref, rate, wall_s, cores = oracle_rate(canvas, cams, args.cpu_seconds)
+        px, ref, rate, wall_s, cores, counts = oracle_rate(canvas, cams, args.cpu_seconds)
         img = out.cpu().numpy().astype(np.float64)[px]
         err = np.abs(img - ref).max(axis=1)
         line["cpu_baseline"] = {"value": rate, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
@@ -372,7 +398,14 @@ def main():
         for name, w in walks.items():
             w["max_err_vs_oracle"] = float(np.abs(w.pop("image").cpu().numpy().astype(np.float64)[px] - ref).max())
             w["Mrays_s"] = rays / (w.pop("ms") * 1e-3) / 1e6
+            # ray-angle error against the ray's length in the canvas and the cells it crossed (oracle sample)
+            a = w.pop("angles")[px]
+            w["angle_vs_length_m"] = binned(a, counts["length"], [1e-3, 1e-2, 1e-1, 1, 10, 100, 1e3, 1e4, 1e5])
+            w["angle_vs_cells"] = binned(a, counts["steps"], [1, 10, 100, 1000, 10000, 100000])
         line["paper_fp32_walks"] = walks
+        # the oracle on one core (a smaller sample; the all-core figure above is the baseline)
+        _, _, rate1, wall1, _, _ = oracle_rate(canvas, cams, max(2.0, args.cpu_seconds / 3), seed=54321, threads=1)
+        line["cpu_baseline_1core"] = {"value": rate1, "unit": "Mrays/s", "cores": 1, "seconds": round(wall1, 1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -40,6 +40,7 @@ extern "C" {
 #define CANVOX_PREC_FP32 2  /* plain FP32 in canvas coordinates (the failing baseline of Sec. 6.3) */
 #define CANVOX_PREC_CELL32 3  /* the paper's FP32 cell-local walk, p' s + c per step (Sec. 6.2-6.3) */
 #define CANVOX_PREC_WORLD32 4 /* the same walk with the position in FP32 canvas coordinates (Sec. 6.3 comparison) */
+#define CANVOX_PREC_CELL16 5  /* the cell-local walk with binary16 geometry (the half-precision remark of Sec. 6.3) */
 
 /*
  * One view (Sec. 6.1: the eye position is kept in FP64 canvas coordinates so
@@ -96,7 +97,7 @@ typedef struct canvox_camera {
  *   err_budget    : per-ray bound on the colour error the FP32 boundaries may add before
  *                   the remaining boundaries are taken in FP64 (mixed precision only).
  *   step_count    : optional device int32 per output pixel: leaves visited by its ray.
- *   angle_deg     : optional device float per output pixel (CELL32 / WORLD32 only): angle in degrees
+ *   angle_deg     : optional device float per output pixel (CELL32 / WORLD32 / CELL16 only): angle in degrees
  *                   between the initial ray direction and the line from the eye to the ray's final
  *                   position (the ray-angle error of Sec. 6.3).
  */
@@ -217,6 +218,33 @@ int canvox_octree_hash(uint64_t* host_hash, uint64_t* device_hash);
  * best is not NULL.
  */
 int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, canvox_render_opts* best);
+
+/*
+ * Measurement helpers (the paper reports no profile; these give the figures the
+ * traversal is measured against). All are synchronous.
+ *
+ * canvox_footprint: the distinct records and stored leaves that the rays of these
+ * views read, i.e. the compulsory bytes of a render from a cold cache
+ * (32 * records + 8 * leaves). Marked by the plain FP64 traversal (leaf located
+ * from the root each step, so every ancestor of every visited leaf counts once),
+ * with the default t_min and no step limit. Needs an uploaded canvas; overwrites
+ * the counters that canvox_get_stats reports. Temporary device memory: one bit per
+ * record and per leaf.
+ */
+int canvox_footprint(const canvox_camera* cams, int32_t n_views, void* stream, int64_t* n_records,
+                     int64_t* n_leaves);
+
+/*
+ * canvox_probe_l2_gather: bandwidth of random 32-byte sector gathers served by L2
+ * (loads that bypass L1, from a buffer of buffer_bytes rounded down to a power of
+ * two; 0 = half the device's L2), in GB/s counted at 32 bytes per gather. The
+ * access pattern of the record and leaf loads with DRAM taken out. buffer_bytes
+ * in [32 KiB, 64 GiB] (or 0), else CANVOX_ERR_INVALID_ARG.
+ */
+int canvox_probe_l2_gather(int64_t buffer_bytes, double* sector_gbs);
+
+/* canvox_probe_fp64: FP64 FMA throughput of the device (independent chains), GFLOP/s (2 per FMA). */
+int canvox_probe_fp64(double* gflops);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* canvox_last_error(void);

@@ -36,6 +36,10 @@ def lib():
                                         ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]
         L.oracle_trace_rays.restype = ctypes.c_int64
+        L.oracle_footprint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+        L.oracle_footprint.restype = ctypes.c_int64
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int32
         _lib = L
@@ -104,3 +108,25 @@ def trace_rays(canvas, origins, directions, background=(0, 0, 0, 0), t_min=T_MIN
     if rc != 0:
         raise RuntimeError(f"oracle_trace_rays returned {rc}")
     return (out, ic, dc) if counters else out
+
+
+def footprint(canvas, cams, t_min=T_MIN_DEFAULT, threads=0):
+    """Records and stored leaves the traversal reads for every pixel of these views.
+
+    Returns (rec_mark bool [n_records], leaf_mark bool [n_leaves], rgba [n_pixels, 4]).
+    """
+    nodes, leaves = _pools(canvas.nodes, canvas.leaves)
+    cams = np.ascontiguousarray(cams)
+    n_views = cams.shape[0]
+    n = 0
+    for c in cams:
+        n = max(n, int(c["out_offset_px"]) + int(c["width"]) * int(c["height"]))
+    out = np.empty((max(n, 1), 4), dtype=np.float64)
+    rm = np.zeros(max(nodes.shape[0], 1), dtype=np.uint8)
+    lm = np.zeros(max(leaves.shape[0], 1), dtype=np.uint8)
+    rc = lib().oracle_footprint(nodes.ctypes.data, leaves.ctypes.data, int(canvas.depth), float(canvas.extent),
+                                cams.ctypes.data if n_views else None, int(n_views), float(t_min), out.ctypes.data,
+                                rm.ctypes.data, lm.ctypes.data, int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_footprint returned {rc}")
+    return rm[:nodes.shape[0]].astype(bool), lm[:canvas.n_leaves].astype(bool), out[:n]

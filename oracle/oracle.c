@@ -13,8 +13,8 @@
  *   sigma and colour c are piecewise constant over the octree leaves. The pixel
  *   is the emission-absorption integral evaluated exactly per leaf segment:
  *       C += T (1 - exp(-sigma l)) c,   T *= exp(-sigma l),
- *   front to back, stopping when T < T_min or at the canvas exit (Sec. 6.2:
- *   "terminates after accumulating full opacity or exits the canvas"), and
+ *   front to back, stopping when T < T_min or at the canvas exit (Sec. 6.2: a
+ *   ray ends once it is opaque or leaves the canvas), and
  *   out = (C + T bg.rgb, 1 - T).
  *
  * How: every step locates the leaf that holds the ray just after the current
@@ -104,7 +104,8 @@ typedef struct {
 
 /* Render one ray; writes rgba[4] and the counters. */
 static void trace(const otree *T, const double o[3], const double d[3], const float bg[4],
-                  double t_min, int64_t max_steps, double rgba[4], ocount *cnt) {
+                  double t_min, int64_t max_steps, double rgba[4], ocount *cnt,
+                  unsigned char *rec_mark, unsigned char *leaf_mark) {
     const double E = T->extent, h = 0.5 * E;
     memset(cnt, 0, sizeof(*cnt));
     /* clip to the canvas: inside on axis a just after t iff enter_a <= t < exit_a */
@@ -142,6 +143,12 @@ static void trace(const otree *T, const double o[3], const double d[3], const fl
                 }
                 w = hw;
                 path[L++] = k;
+                if (rec_mark) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                    rec_mark[rec] = 1;
+                }
                 slot = T->nodes[8 * (int64_t)rec + k];
                 if (slot <= 0) break;
                 rec = slot;
@@ -169,6 +176,12 @@ static void trace(const otree *T, const double o[3], const double d[3], const fl
                 const uint16_t *v = T->leaves + 4 * (int64_t)(-slot - 1);
                 double sg = half_to_double(v[3]);
                 cnt->leaf_loads += 1;
+                if (leaf_mark) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                    leaf_mark[-slot - 1] = 1;
+                }
                 if (sg > 0.0) {
                     double a = -expm1(-sg * l);
                     for (int c = 0; c < 3; ++c) C[c] += Tr * a * half_to_double(v[c]);
@@ -184,17 +197,17 @@ static void trace(const otree *T, const double o[3], const double d[3], const fl
 }
 
 /*
- * Render the listed output pixels (or, when px_idx is NULL, every pixel of
+ * oracle_render: render the listed output pixels (or, when px_idx is NULL, every pixel of
  * every view, indexed by output pixel). out_rgba: n x 4 doubles. Optional
  * counters: icount n x 3 (steps, slot reads from the LCA, leaf loads) and
  * dcount n x 2 (sum of crossed cell widths, ray length in the canvas).
  * Returns 0, -1 for bad arguments, or the number of rays that hit the
  * step guard (an oracle bug; those pixels are NaN).
  */
-int64_t oracle_render(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
-                      const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
-                      double t_min, int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount,
-                      int32_t n_threads) {
+static int64_t render_pixels(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
+                             const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
+                             double t_min, int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount,
+                             int32_t n_threads, unsigned char *rec_mark, unsigned char *leaf_mark) {
     if (!nodes || depth < 1 || depth > 30 || !(extent > 0.0) || n_views < 0 || (n_views && !cams) || !out_rgba)
         return -1;
     otree T = {nodes, leaves, depth, extent};
@@ -228,13 +241,36 @@ int64_t oracle_render(const int32_t *nodes, const uint16_t *leaves, int32_t dept
             double f[3], u[3], r[3], d[3];
             camera_frame(c, f, u, r);
             pixel_ray(c, f, u, r, local % c->width, local / c->width, d);
-            trace(&T, c->eye, d, c->background, t_min, max_steps, out, &cnt);
+            trace(&T, c->eye, d, c->background, t_min, max_steps, out, &cnt, rec_mark, leaf_mark);
             if (cnt.guard) { out[0] = out[1] = out[2] = out[3] = NAN; bad += 1; }
         }
         if (icount) { icount[3 * q] = cnt.steps; icount[3 * q + 1] = cnt.reads; icount[3 * q + 2] = cnt.leaf_loads; }
         if (dcount) { dcount[2 * q] = cnt.sum_width; dcount[2 * q + 1] = cnt.length; }
     }
     return bad;
+}
+
+int64_t oracle_render(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
+                      const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
+                      double t_min, int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount,
+                      int32_t n_threads) {
+    return render_pixels(nodes, leaves, depth, extent, cams, n_views, px_idx, n_px, t_min, max_steps, out_rgba,
+                         icount, dcount, n_threads, NULL, NULL);
+}
+
+/*
+ * Render every pixel (out_rgba: one row of 4 doubles per output pixel) and
+ * mark the records this traversal reads (every record on the root-to-leaf path
+ * of every step) and the stored leaves it loads: rec_mark[n_records] and
+ * leaf_mark[n_leaves] bytes, set to 1. This is the footprint of the traversal
+ * (the distinct data a render from a cold cache must read).
+ */
+int64_t oracle_footprint(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
+                         const ocam *cams, int32_t n_views, double t_min, double *out_rgba,
+                         unsigned char *rec_mark, unsigned char *leaf_mark, int32_t n_threads) {
+    if (!rec_mark || !leaf_mark) return -1;
+    return render_pixels(nodes, leaves, depth, extent, cams, n_views, NULL, 0, t_min, 0, out_rgba, NULL, NULL,
+                         n_threads, rec_mark, leaf_mark);
 }
 
 /* Trace explicit rays (origin, direction not necessarily unit). For tests of single rays. */
@@ -250,7 +286,7 @@ int64_t oracle_trace_rays(const int32_t *nodes, const uint16_t *leaves, int32_t 
         double nn = sqrt(dot3(d, d));
         for (int a = 0; a < 3; ++a) d[a] /= nn;
         ocount cnt;
-        trace(&T, orig + 3 * q, d, bg, t_min, max_steps, out_rgba + 4 * q, &cnt);
+        trace(&T, orig + 3 * q, d, bg, t_min, max_steps, out_rgba + 4 * q, &cnt, NULL, NULL);
         if (cnt.guard) bad += 1;
         if (icount) { icount[3 * q] = cnt.steps; icount[3 * q + 1] = cnt.reads; icount[3 * q + 2] = cnt.leaf_loads; }
         if (dcount) { dcount[2 * q] = cnt.sum_width; dcount[2 * q + 1] = cnt.length; }

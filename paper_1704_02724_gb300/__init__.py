@@ -13,6 +13,7 @@ from .canvox import (  # noqa: F401
     PREC_FP32,
     PREC_CELL32,
     PREC_WORLD32,
+    PREC_CELL16,
     lib,
     upload_octree,
     render,
@@ -21,6 +22,9 @@ from .canvox import (  # noqa: F401
     get_stats,
     octree_hash,
     autotune,
+    footprint,
+    probe_l2_gather,
+    probe_fp64,
     default_opts,
     last_error,
     release,

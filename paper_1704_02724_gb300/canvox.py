@@ -28,6 +28,7 @@ PREC_FP64 = 1
 PREC_FP32 = 2
 PREC_CELL32 = 3
 PREC_WORLD32 = 4
+PREC_CELL16 = 5
 
 # canvox_camera: 136 bytes (eye, right, up, forward: FP64[3]; tan; width, height; offset; background FP32[4])
 CAMERA_BYTES = 136
@@ -94,6 +95,12 @@ def lib():
         L.canvox_octree_hash.restype = ctypes.c_int
         L.canvox_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(Opts)]
         L.canvox_autotune.restype = ctypes.c_int
+        L.canvox_footprint.argtypes = [vp, i32, vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.canvox_footprint.restype = ctypes.c_int
+        L.canvox_probe_l2_gather.argtypes = [i64, ctypes.POINTER(ctypes.c_double)]
+        L.canvox_probe_l2_gather.restype = ctypes.c_int
+        L.canvox_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        L.canvox_probe_fp64.restype = ctypes.c_int
         L.canvox_last_error.argtypes = []
         L.canvox_last_error.restype = ctypes.c_char_p
         L.canvox_release.argtypes = []
@@ -217,6 +224,29 @@ def autotune(cams, stream=None):
     o = Opts()
     _check(lib().canvox_autotune(cams.ctypes.data, cams.shape[0], _stream_ptr(stream), ctypes.byref(o)))
     return _opts_to_dict(o)
+
+
+def footprint(cams, stream=None):
+    """canvox_footprint: (distinct records, distinct stored leaves) the rays of these views read."""
+    cams = _cams(cams)
+    r, l_ = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().canvox_footprint(cams.ctypes.data if cams.size else None, cams.shape[0], _stream_ptr(stream),
+                                  ctypes.byref(r), ctypes.byref(l_)))
+    return r.value, l_.value
+
+
+def probe_l2_gather(buffer_bytes=0):
+    """canvox_probe_l2_gather: GB/s of random 32-byte sector gathers served by L2."""
+    v = ctypes.c_double()
+    _check(lib().canvox_probe_l2_gather(int(buffer_bytes), ctypes.byref(v)))
+    return v.value
+
+
+def probe_fp64():
+    """canvox_probe_fp64: FP64 FMA GFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().canvox_probe_fp64(ctypes.byref(v)))
+    return v.value
 
 
 def release():

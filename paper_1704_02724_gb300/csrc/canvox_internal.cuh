@@ -105,6 +105,8 @@ struct PlainParams {
     Scratch* scratch;
     int64_t step_limit;
     float t_min;
+    uint32_t* mark_rec;   // footprint bitsets (plain kernel only; null: off): the record holding
+    uint32_t* mark_leaf;  // each located leaf's slot, and each stored leaf loaded
 };
 
 // Launchers (trace_mixed.cu, trace_plain.cu, runtime.cu).
@@ -115,6 +117,11 @@ cudaError_t launch_local32(const PlainParams& p, int precision, long long n_pixe
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, int64_t hi, int level, cudaStream_t s);
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
+cudaError_t probe_l2_gather(int64_t buffer_bytes, double* gbs);
+cudaError_t probe_fp64(double* gflops);
+cudaError_t footprint_finish(const int32_t* nodes, const int64_t* level_begin, int n_levels, uint32_t* rec_bits,
+                             int64_t rec_words, const uint32_t* leaf_bits, int64_t leaf_words,
+                             unsigned long long* d_count, int64_t* n_records, int64_t* n_leaves);
 
 // Host helpers of runtime.cu shared with other entry points.
 int build_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t* total_rays);

@@ -64,6 +64,7 @@ struct Ctx {
     int32_t depth = 0;
     double extent = 0.0;
     unsigned long long host_hash = 0;
+    std::vector<int64_t> level_begin;  // records of level l: [level_begin[l], level_begin[l + 1])
     bool uploaded = false;
     // views: device table and two pinned staging buffers, each guarded by an event
     View* d_views = nullptr;
@@ -224,7 +225,7 @@ int setup_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t
 int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (in) *o = *in;
     else canvox_default_opts(o);
-    if (o->precision < 0 || o->precision > 4) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
+    if (o->precision < 0 || o->precision > 5) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
     if (o->block_threads == 0) o->block_threads = 256;
     if (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)
         return fail(CANVOX_ERR_INVALID_ARG, "block_threads %d (multiple of 32, at most 256)", o->block_threads);
@@ -327,7 +328,7 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
         for (int v = 0; v < n; ++v) {
             p.view = g.d_views + v;
             const long long npx = (long long)views_host[v].width * views_host[v].height;
-            if (o.precision == CANVOX_PREC_CELL32 || o.precision == CANVOX_PREC_WORLD32)
+            if (o.precision == CANVOX_PREC_CELL32 || o.precision == CANVOX_PREC_WORLD32 || o.precision == CANVOX_PREC_CELL16)
                 CK(launch_local32(p, o.precision, npx, s), "single-precision walk launch");
             else
                 CK(launch_plain(p, o.precision, npx, s), "plain kernel launch");
@@ -444,6 +445,7 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     if (dh != hh) return fail(CANVOX_ERR_CUDA, "device copy hash %016llx differs from host %016llx", dh, hh);
     // neighbour links, level by level (breadth-first order keeps each level contiguous)
     CK(cudaMalloc(&g.d_ropes, sizeof(uint2) * 6 * (size_t)n_records), "cudaMalloc(ropes)");
+    g.level_begin.assign(1, 0);
     {
         int64_t lo = 0;
         while (lo < n_records) {
@@ -451,6 +453,7 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
             const int lev = level[(size_t)lo];
             while (hi < n_records && level[(size_t)hi] == lev) ++hi;
             CK(launch_rope_level(g.d_nodes, g.d_ropes, lo, hi, lev, 0), "rope kernel launch");
+            g.level_begin.push_back(hi);
             lo = hi;
         }
         CK(cudaDeviceSynchronize(), "rope build");
@@ -678,6 +681,75 @@ int canvox_autotune(const canvox_camera* cams, int32_t n_views, void* stream, ca
     g.tuned = win;
     g.have_tuned = true;
     if (best) *best = win;
+    return CANVOX_OK;
+}
+
+int canvox_footprint(const canvox_camera* cams, int32_t n_views, void* stream, int64_t* n_records, int64_t* n_leaves) {
+    g_err.clear();
+    if (n_views < 0 || (n_views > 0 && !cams) || !n_records || !n_leaves)
+        return fail(CANVOX_ERR_INVALID_ARG, "null cameras/results or n_views < 0");
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    int rc = ensure_device();
+    if (rc) return rc;
+    canvox_render_opts o;
+    builtin_defaults(&o);
+    if ((rc = resolve_opts(&o, &o))) return rc;
+    std::vector<View> views((size_t)(n_views > 0 ? n_views : 1));
+    int64_t total_rays = 0;
+    if (n_views > 0 && (rc = setup_views(cams, n_views, o.tile_w, views.data(), &total_rays))) return rc;
+    if ((rc = ensure_views(n_views > 0 ? n_views : 1)) || (rc = ensure_scratch(1))) return rc;
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t rec_words = (g.n_rec + 31) / 32, leaf_words = (g.n_leaf + 31) / 32;
+    uint32_t* bits = nullptr;
+    CK(cudaMalloc(&bits, sizeof(uint32_t) * (size_t)(rec_words + leaf_words + 4)), "cudaMalloc(footprint)");
+    struct Free {
+        uint32_t* p;
+        ~Free() { cudaFree(p); }
+    } guard{bits};
+    CK(cudaMemset(bits, 0, sizeof(uint32_t) * (size_t)(rec_words + leaf_words + 4)), "cudaMemset(footprint)");
+    if (n_views > 0)
+        CK(cudaMemcpy(g.d_views, views.data(), sizeof(View) * (size_t)n_views, cudaMemcpyHostToDevice), "cudaMemcpy(views)");
+    CK(cudaMemset(g.d_scratch, 0, scratch_bytes(1)), "cudaMemset(scratch)");
+    PlainParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.tree = device_tree();
+    p.scratch = g.d_scratch;
+    p.step_limit = o.step_limit;
+    p.t_min = o.t_min;
+    p.mark_rec = bits;
+    p.mark_leaf = bits + rec_words;
+    for (int v = 0; v < n_views; ++v) {
+        p.view = g.d_views + v;
+        CK(launch_plain(p, CANVOX_PREC_FP64, (long long)views[v].width * views[v].height, s), "footprint launch");
+    }
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize(footprint)");
+    unsigned long long* d_count = reinterpret_cast<unsigned long long*>(bits + rec_words + leaf_words);
+    if (reinterpret_cast<uintptr_t>(d_count) % 8) d_count = reinterpret_cast<unsigned long long*>(bits + rec_words + leaf_words + 1);
+    CK(footprint_finish(g.d_nodes, g.level_begin.data(), (int)g.level_begin.size() - 1, bits, rec_words,
+                        bits + rec_words, leaf_words, d_count, n_records, n_leaves), "footprint count");
+    return CANVOX_OK;
+}
+
+int canvox_probe_l2_gather(int64_t buffer_bytes, double* sector_gbs) {
+    g_err.clear();
+    if (!sector_gbs || buffer_bytes < 0 || buffer_bytes > ((int64_t)1 << 36))
+        return fail(CANVOX_ERR_INVALID_ARG, "buffer_bytes %lld out of range", (long long)buffer_bytes);
+    int dev = 0, l2 = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (buffer_bytes == 0) {
+        CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "cudaDeviceGetAttribute(L2)");
+        buffer_bytes = l2 / 2;
+    }
+    if (buffer_bytes < (1 << 15)) return fail(CANVOX_ERR_INVALID_ARG, "buffer_bytes below 32 KiB");
+    CK(probe_l2_gather(buffer_bytes, sector_gbs), "L2 gather probe");
+    return CANVOX_OK;
+}
+
+int canvox_probe_fp64(double* gflops) {
+    g_err.clear();
+    if (!gflops) return fail(CANVOX_ERR_INVALID_ARG, "null result");
+    CK(probe_fp64(gflops), "FP64 probe");
     return CANVOX_OK;
 }
 

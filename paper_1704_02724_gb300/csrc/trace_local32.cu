@@ -12,12 +12,19 @@
 // coordinates and cell planes rounded to FP32 (the paper's "canvas coordinate"
 // comparison); the drift then scales with the coordinates, not the cells.
 //
-// Both write, per pixel and on request, the angle between the initial ray
+// Cell-local in half precision (CANVOX_PREC_CELL16): the cell-local walk with
+// every geometric quantity (p, d, t, p', the scale and offset) in IEEE binary16,
+// eps = 2^-10; the section closes by noting that the cell-local frame would let
+// a half-precision GPU trace the canvas. Compositing stays in FP32.
+//
+// All three write, per pixel and on request, the angle between the initial ray
 // direction and the line from the eye to the ray's final position (degrees).
 // The eye and the pixel ray are the FP64 camera model; the start leaf is
 // located in FP64 as in the other kernels; leaves are located from the root
 // each step from integer coordinates, and by the FP32 position below the
 // level of the cell the ray leaves.
+#include <cuda_fp16.h>
+
 #include "canvox_internal.cuh"
 
 namespace canvox {
@@ -28,6 +35,28 @@ __device__ __forceinline__ float h2f32(unsigned short h) {
     return __int_as_float(__float_as_int(m) | (int)((h & 0x8000u) << 16));
 }
 __device__ __forceinline__ double p2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// Geometry arithmetic of a walk: FP32 or binary16, every operation rounded to nearest.
+struct Geo32 {
+    using T = float;
+    static __device__ __forceinline__ T from_d(double x) { return (float)x; }
+    static __device__ __forceinline__ T from_f(float x) { return x; }
+    static __device__ __forceinline__ float f(T x) { return x; }
+    static __device__ __forceinline__ T add(T a, T b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ T mul(T a, T b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ T div(T a, T b) { return __fdiv_rn(a, b); }
+};
+struct Geo16 {
+    using T = __half;
+    static __device__ __forceinline__ T from_d(double x) { return __double2half(x); }
+    static __device__ __forceinline__ T from_f(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float f(T x) { return __half2float(x); }
+    static __device__ __forceinline__ T add(T a, T b) { return __hadd(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return __hsub(a, b); }
+    static __device__ __forceinline__ T mul(T a, T b) { return __hmul(a, b); }
+    static __device__ __forceinline__ T div(T a, T b) { return __hdiv(a, b); }
+};
 
 struct Local32Count {
     unsigned long long steps, leaf_loads, rec_loads;
@@ -52,8 +81,9 @@ __device__ __forceinline__ int32_t locate_int(const Tree& T, const unsigned c[3]
     }
 }
 
-template <bool kCellLocal>
+template <bool kCellLocal, typename G>
 __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
+    using GT = typename G::T;
     const View& V = *P.view;
     const Tree& T = P.tree;
     const int i = (int)(idx % V.width), j = (int)(idx / V.width);
@@ -99,16 +129,17 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             if (slot <= 0) break;
             rec = slot;
         }
-        const float d[3] = {(float)d64[0], (float)d64[1], (float)d64[2]};
-        float p[3];
+        const GT d[3] = {G::from_d(d64[0]), G::from_d(d64[1]), G::from_d(d64[2])};
+        const GT g_half = G::from_f(0.5f), g_mhalf = G::from_f(-0.5f), g_two = G::from_f(2.0f);
+        GT p[3];
         for (int a = 0; a < 3; ++a) {
             const double x = fma(t0, d64[a], o[a]);
             if (kCellLocal) {
                 const double w = T.extent * p2d(-L);
                 const double centre = fma((double)c[a] + 0.5, w, -T.half);
-                p[a] = (float)((x - centre) / w);  // start point in the cell frame: the error e0
+                p[a] = G::from_d((x - centre) / w);  // start point in the cell frame: the error e0
             } else {
-                p[a] = (float)x;                   // start point snapped to FP32 canvas coordinates
+                p[a] = G::from_d(x);                 // start point snapped to FP32 canvas coordinates
             }
         }
         double X[3] = {fma(t0, d64[0], o[0]), fma(t0, d64[1], o[1]), fma(t0, d64[2], o[2])};
@@ -122,18 +153,19 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             const double w64 = T.extent * p2d(-L);
             const float w = (float)w64;
             // exit face: t_a = (face_a - p_a) / d_a, the nearest one
-            float te = __int_as_float(0x7F800000);
+            GT te = G::from_f(0.0f);
+            float tef = __int_as_float(0x7F800000);
             int ax = -1;
             for (int a = 0; a < 3; ++a) {
-                if (d[a] == 0.0f) continue;
-                float face;
-                if (kCellLocal) face = d[a] > 0.0f ? 0.5f : -0.5f;
-                else face = (float)fma((double)(c[a] + (d[a] > 0.0f ? 1u : 0u)), w64, -T.half);
-                const float ta = __fdiv_rn(__fsub_rn(face, p[a]), d[a]);
-                if (ta < te) { te = ta; ax = a; }
+                if (G::f(d[a]) == 0.0f) continue;
+                GT face;
+                if (kCellLocal) face = G::f(d[a]) > 0.0f ? g_half : g_mhalf;
+                else face = G::from_d(fma((double)(c[a] + (G::f(d[a]) > 0.0f ? 1u : 0u)), w64, -T.half));
+                const GT ta = G::div(G::sub(face, p[a]), d[a]);
+                if (G::f(ta) < tef) { te = ta; tef = G::f(ta); ax = a; }
             }
             if (ax < 0) break;
-            const float ell = kCellLocal ? __fmul_rn(fmaxf(te, 0.0f), w) : fmaxf(te, 0.0f);
+            const float ell = kCellLocal ? __fmul_rn(fmaxf(tef, 0.0f), w) : fmaxf(tef, 0.0f);
             if (slot < 0) {
                 const uint2 q = __ldg(T.leaves + (-(long long)slot - 1));
                 leaf_loads += 1;
@@ -147,14 +179,14 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
                 }
             }
             // exit point p' = p + t d (the exit axis on its face)
-            float pe[3];
-            for (int a = 0; a < 3; ++a) pe[a] = __fadd_rn(p[a], __fmul_rn(te, d[a]));
-            if (kCellLocal) pe[ax] = d[ax] > 0.0f ? 0.5f : -0.5f;
+            GT pe[3];
+            for (int a = 0; a < 3; ++a) pe[a] = G::add(p[a], G::mul(te, d[a]));
+            if (kCellLocal) pe[ax] = G::f(d[ax]) > 0.0f ? g_half : g_mhalf;
             // final position so far, in FP64 canvas coordinates
             for (int a = 0; a < 3; ++a)
-                X[a] = kCellLocal ? fma((double)c[a] + 0.5 + (double)pe[a], w64, -T.half) : (double)pe[a];
+                X[a] = kCellLocal ? fma((double)c[a] + 0.5 + (double)G::f(pe[a]), w64, -T.half) : (double)G::f(pe[a]);
             if (Tr < P.t_min) break;
-            const unsigned up = d[ax] > 0.0f ? 1u : 0u;
+            const unsigned up = G::f(d[ax]) > 0.0f ? 1u : 0u;
             const unsigned cn = up ? c[ax] + 1u : c[ax] - 1u;
             if ((cn >> L) != 0u) break;  // leaves the canvas
             unsigned cc[3] = {c[0], c[1], c[2]};
@@ -163,9 +195,9 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             int32_t pr;
             slot = locate_int(T, cc, L, &Ln, &pr, &kk, &rec_loads);
             // position in the frame of the same-level neighbour (its centre is one cell further on ax)
-            float q[3];
+            GT q[3];
             for (int a = 0; a < 3; ++a) q[a] = pe[a];
-            if (kCellLocal) q[ax] = up ? -0.5f : 0.5f;
+            if (kCellLocal) q[ax] = up ? g_mhalf : g_half;
             int Lc = L;
             while (slot > 0) {
                 // finer neighbour: near side on the exit axis, FP32 position on the others
@@ -177,12 +209,12 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
                     if (a == ax) {
                         b = up ? 0u : 1u;
                     } else if (kCellLocal) {
-                        b = q[a] > 0.0f || (q[a] == 0.0f && d[a] >= 0.0f);
+                        b = G::f(q[a]) > 0.0f || (G::f(q[a]) == 0.0f && G::f(d[a]) >= 0.0f);
                     } else {
-                        const float M = (float)fma((double)(2u * cc[a] + 1u), wc, -T.half);
-                        b = q[a] > M || (q[a] == M && d[a] >= 0.0f);
+                        const float M = G::f(G::from_d(fma((double)(2u * cc[a] + 1u), wc, -T.half)));
+                        b = G::f(q[a]) > M || (G::f(q[a]) == M && G::f(d[a]) >= 0.0f);
                     }
-                    if (kCellLocal) q[a] = __fsub_rn(__fmul_rn(2.0f, q[a]), b ? 0.5f : -0.5f);
+                    if (kCellLocal) q[a] = G::sub(G::mul(g_two, q[a]), b ? g_half : g_mhalf);
                     cc[a] = 2u * cc[a] + b;
                     k |= (int)b << a;
                 }
@@ -193,13 +225,14 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             }
             if (kCellLocal && Ln < L) {
                 // coarser neighbour: p s + c with s = 2^(Ln - L) and c the centre offset (exact)
-                const float s = __int_as_float((127 + (Ln - L)) << 23);
+                const double s64 = p2d(Ln - L);
+                const GT s = G::from_d(s64);  // binary16: 0 below 2^-25 (the offset alone then places the point)
                 for (int a = 0; a < 3; ++a) {
                     const unsigned cp = cc[a] >> (L - Ln);
-                    const double off = ((double)cc[a] + 0.5) * (double)s - ((double)cp + 0.5);
-                    q[a] = __fadd_rn(__fmul_rn(q[a], s), (float)off);
+                    const double off = ((double)cc[a] + 0.5) * s64 - ((double)cp + 0.5);
+                    q[a] = G::add(G::mul(q[a], s), G::from_d(off));
                 }
-                if (kCellLocal) q[ax] = up ? -0.5f : 0.5f;
+                if (kCellLocal) q[ax] = up ? g_mhalf : g_half;
             }
             const int sh = Lc - Ln;
             for (int a = 0; a < 3; ++a) {
@@ -226,12 +259,12 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
     return Local32Count{(unsigned long long)steps, leaf_loads, rec_loads};
 }
 
-template <bool kCellLocal>
+template <bool kCellLocal, typename G>
 __global__ void __launch_bounds__(256) local32_kernel(PlainParams P, long long n_pixels) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     Local32Count c = {0ull, 0ull, 0ull};
     const bool valid = idx < n_pixels;
-    if (valid) c = local32_ray<kCellLocal>(P, idx);
+    if (valid) c = local32_ray<kCellLocal, G>(P, idx);
     unsigned long long vals[5] = {valid ? 1ull : 0ull, c.steps, 0ull, c.leaf_loads, c.rec_loads};
     for (int q = 0; q < 5; ++q) {
         unsigned long long s = vals[q];
@@ -246,8 +279,9 @@ cudaError_t launch_local32(const PlainParams& p, int precision, long long n_pixe
     if (n_pixels <= 0) return cudaSuccess;
     const long long grid = (n_pixels + 255) / 256;
     if (grid > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-    if (precision == CANVOX_PREC_CELL32) local32_kernel<true><<<(unsigned)grid, 256, 0, s>>>(p, n_pixels);
-    else local32_kernel<false><<<(unsigned)grid, 256, 0, s>>>(p, n_pixels);
+    if (precision == CANVOX_PREC_CELL32) local32_kernel<true, Geo32><<<(unsigned)grid, 256, 0, s>>>(p, n_pixels);
+    else if (precision == CANVOX_PREC_CELL16) local32_kernel<true, Geo16><<<(unsigned)grid, 256, 0, s>>>(p, n_pixels);
+    else local32_kernel<false, Geo32><<<(unsigned)grid, 256, 0, s>>>(p, n_pixels);
     return cudaGetLastError();
 }
 

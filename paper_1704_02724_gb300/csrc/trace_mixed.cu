@@ -50,13 +50,8 @@ constexpr int kMaxFrameBits = 22;                   // a frame spans at most 22 
 
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
-// IEEE binary16 bits -> float, exactly, on the integer and FP32 pipes (no conversion
-// instruction): the 15 magnitude bits shifted to the FP32 field positions read as
-// 2^-112 times the value (normals and subnormals alike); the sign is copied.
-__device__ __forceinline__ float half_bits_to_float(unsigned h) {
-    const float m = __int_as_float((int)((h & 0x7FFFu) << 13)) * 5.192296858534828e+33f;  // * 2^112
-    return __int_as_float(__float_as_int(m) | (int)((h & 0x8000u) << 16));
-}
+// IEEE binary16 bits -> float (exact: every half is a float).
+__device__ __forceinline__ float half_bits_to_float(unsigned h) { return __half2float(__ushort_as_half((unsigned short)h)); }
 __device__ __forceinline__ float hsig(uint2 v) { return half_bits_to_float(v.y >> 16); }
 __device__ __forceinline__ float hlo(unsigned w) { return half_bits_to_float(w & 0xFFFFu); }
 __device__ __forceinline__ float hhi(unsigned w) { return half_bits_to_float(w >> 16); }

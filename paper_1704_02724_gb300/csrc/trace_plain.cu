@@ -38,6 +38,13 @@ struct Num<float> {
 
 __device__ __forceinline__ float h2f(unsigned short h) { return __half2float(__ushort_as_half(h)); }
 
+// Set bit i of a footprint bitset (read through L2 first: most bits are already set).
+__device__ __forceinline__ void mark_bit(uint32_t* bits, long long i) {
+    const uint32_t m = 1u << (i & 31);
+    uint32_t* w = bits + (i >> 5);
+    if (!(__ldcg(w) & m)) atomicOr(w, m);
+}
+
 struct PlainCount {
     unsigned long long steps, leaf_loads, rec_loads;
 };
@@ -113,6 +120,7 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
                     break;
                 }
             }
+            if (P.mark_rec) mark_bit(P.mark_rec, rec);
             const int L = lev + 1;
             const R w = E * N::pow2(-L);
             R te = N::inf();
@@ -127,6 +135,7 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
             if (slot < 0) {
                 const uint2 q = __ldg(T.leaves + (-(long long)slot - 1));
                 leaf_loads += 1;
+                if (P.mark_leaf) mark_bit(P.mark_leaf, -(long long)slot - 1);
                 const R s = (R)h2f((unsigned short)(q.y >> 16));
                 if (s > (R)0) {
                     const R l = te - t;
@@ -147,7 +156,7 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
     out.z = (float)(C[2] + Tr * (R)V.bg[2]);
     out.w = (float)(1 - Tr);
     const long long pix = V.out_offset + idx;
-    P.out[pix] = out;
+    if (P.out) P.out[pix] = out;
     if (P.step_count) P.step_count[pix] = steps;
     return PlainCount{(unsigned long long)steps, leaf_loads, rec_loads};
 }

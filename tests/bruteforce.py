@@ -55,8 +55,9 @@ def _tree_depth(nodes):
     return int(depth.max()) + 1
 
 
-def march(grid, o, d, bg=(0.0, 0.0, 0.0, 0.0), t_min=0.0):
-    """Returns (rgba, steps, reads): steps = leaves entered, reads = slot reads with a perfect stack."""
+def march(grid, o, d, bg=(0.0, 0.0, 0.0, 0.0), t_min=0.0, visited=None):
+    """Returns (rgba, steps, reads): steps = leaves entered, reads = slot reads with a perfect stack.
+    With a list `visited`, appends the id (record * 8 + child) of every leaf entered."""
     o = [float(x) for x in o]
     bg = [float(x) for x in np.asarray(bg, dtype=np.float32)]  # the camera record stores FP32 background
     d = np.asarray(d, dtype=np.float64)
@@ -91,6 +92,8 @@ def march(grid, o, d, bg=(0.0, 0.0, 0.0, 0.0), t_min=0.0):
             idx = [min(grid.N - 1, max(0, int(math.floor((o[a] + tm * d[a] + h) / w)))) for a in range(3)]
             lid = int(grid.leaf[idx[0], idx[1], idx[2]])
             if lid != prev_leaf:
+                if visited is not None:
+                    visited.append(lid)
                 p = grid.paths[lid]
                 common = 0
                 if prev_path is not None:

@@ -230,3 +230,38 @@ def test_stamp_canvas_matches_bruteforce():
         ref, steps, reads = march(grid, o[i], d[i])
         np.testing.assert_allclose(got[i], ref, rtol=0, atol=1e-12)
         assert (ic[i, 0], ic[i, 1]) == (steps, reads)
+
+
+def test_footprint_matches_bruteforce():
+    """The records and stored leaves the oracle marks = the root-to-leaf paths of the leaves the dense-grid
+    marcher enters (no tree descent there), over every pixel of a view."""
+    cv = rt.random_tree(5, seed=41, p_refine=0.5)
+    eye = np.array([1.1, -0.6, 1.5])
+    cam = synth.look_at_camera(eye, [0.02, 0.07, -0.04], [0, 1, 0], math.tan(math.radians(30)), 21, 13, 0,
+                               (0, 0, 0, 1))
+    cams = synth.cameras_array([cam])
+    rm, lm, img = oracle.footprint(cv, cams, t_min=0.0)
+    np.testing.assert_allclose(img, oracle.render(cv, cams, t_min=0.0), rtol=0, atol=0)
+    grid = DenseGrid(cv)
+    W, H, t = 21, 13, float(cam["tan_half_fov_y"])
+    f, r, u = cam["forward"], cam["right"], cam["up"]
+    rec_ref = np.zeros(cv.nodes.shape[0], dtype=bool)
+    leaf_ref = np.zeros(cv.n_leaves, dtype=bool)
+    for j in range(H):
+        for i in range(W):
+            x = (2 * (i + 0.5) / W - 1) * t * W / H
+            y = (1 - 2 * (j + 0.5) / H) * t
+            seen = []
+            march(grid, eye, f + x * r + y * u, visited=seen)
+            for lid in seen:
+                rec = 0
+                for k in grid.paths[lid]:
+                    rec_ref[rec] = True
+                    v = int(cv.nodes[rec, k])
+                    if v > 0:
+                        rec = v
+                    elif v < 0:
+                        leaf_ref[-v - 1] = True
+    assert rec_ref.sum() > 10 and leaf_ref.sum() > 10
+    np.testing.assert_array_equal(rm, rec_ref)
+    np.testing.assert_array_equal(lm, leaf_ref)

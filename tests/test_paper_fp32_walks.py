@@ -1,7 +1,8 @@
 """The paper's single-precision walks on a GPU (Sec. 6.2-6.3; Fig. rayAngleError and the
 canvas-vs-cell coordinate comparison): the cell-local FP32 walk keeps the ray-angle error
-small at any depth, the same walk in FP32 canvas coordinates drifts, and the library's
-mixed-precision path meets the 1e-5 bar where neither does."""
+small at any depth, the same walk in FP32 canvas coordinates drifts, the cell-local walk
+in binary16 stays within the same bound with eps = 2^-10, and the library's
+mixed-precision path meets the 1e-5 bar where none of them does."""
 import math
 
 import numpy as np
@@ -17,6 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 EPS = 2.0 ** -23   # the paper's machine epsilon for FP32
+EPS16 = 2.0 ** -10  # binary16 (the half-precision remark of Sec. 6.3)
 
 
 def _angles(cv, cams, key, prec):
@@ -37,6 +39,14 @@ def test_cell_local_walk_shallow_canvas():
     e0 = math.sqrt(3) * 2.0 ** -25 * 2.0 ** -1
     bound = math.degrees(math.asin(math.sqrt(2) * (e0 / 1.5 + 7.5 * EPS)))
     assert np.max(ang) <= bound
+    # the same walk in binary16: the same bound with eps = 2^-10 (and e0 of a binary16 start point)
+    img16, ang16 = _angles(cv, cams, "c0", cx.PREC_CELL16)
+    assert np.all(np.isfinite(img16)) and np.all(np.isfinite(ang16))
+    e0_16 = math.sqrt(3) * 2.0 ** -12 * 2.0 ** -1
+    bound16 = math.degrees(math.asin(math.sqrt(2) * (e0_16 / 1.5 + 7.5 * EPS16)))
+    assert np.max(ang16) <= bound16
+    assert np.max(ang16) > 10 * np.max(ang)
+    assert np.median(np.abs(img16 - ref).max(axis=1)) <= 0.05  # wrong cells only along silhouettes
 
 
 @pytest.mark.parametrize("level", [23, 26])
@@ -57,3 +67,8 @@ def test_angle_error_cell_vs_canvas_coordinates(level):
     # canvas coordinates: the eye and positions snap to FP32 values far coarser than the scene
     assert np.max(a_world) > 100 * np.max(a_cell)
     assert max_err(world, ref) > max_err(cell, ref)
+    # binary16 cell-local walk: the bound with eps = 2^-10 holds at this depth as well
+    _, a16 = _angles(cv, cams, ("deep", level), cx.PREC_CELL16)
+    e0_16 = math.sqrt(3) * 2.0 ** -12 * s
+    bound16 = math.degrees(math.asin(min(1.0, math.sqrt(2) * (e0_16 / s + 7.5 * EPS16))))
+    assert np.all(np.isfinite(a16)) and np.max(a16) <= bound16
