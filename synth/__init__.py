@@ -58,6 +58,8 @@ def lib():
         L.synth_tree_export.restype = ctypes.c_int
         L.synth_tree_sizes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.synth_tree_sizes.restype = None
+        L.synth_tree_set_root_levels.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        L.synth_tree_set_root_levels.restype = ctypes.c_int
         L.synth_set_threads.argtypes = [ctypes.c_int32]
         L.synth_set_threads.restype = None
         L.synth_set_split.argtypes = [ctypes.c_int32]
@@ -104,8 +106,9 @@ class Canvas:
         return int(self.leaves.shape[0])
 
 
-def stamp_canvas(depth, extent, centers, radii, rgba):
-    """Build a canvas from spherical stamps applied in order."""
+def stamp_canvas(depth, extent, centers, radii, rgba, root_levels=1):
+    """Build a canvas from spherical stamps applied in order. root_levels = 2 keeps the top two
+    levels refined everywhere: the 4^3 array of octree roots (the level-2 cells) of Sec. 4."""
     L = lib()
     centers = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
     radii = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
@@ -116,6 +119,8 @@ def stamp_canvas(depth, extent, centers, radii, rgba):
     if not h:
         raise ValueError("bad depth/extent")
     try:
+        if root_levels != 1 and L.synth_tree_set_root_levels(h, int(root_levels)) != 0:
+            raise ValueError("root_levels must be in [1, depth)")
         if n:
             rc = L.synth_tree_stamp_spheres(h, n, centers.ctypes.data, radii.ctypes.data, rgba.ctypes.data)
             if rc != 0:

@@ -198,6 +198,7 @@ struct Builder {
     std::vector<PNode> P;
     int64_t n_rec = 0, n_leaf = 0;
     int32_t levels = 0;
+    int32_t root_levels = 1;  // levels kept refined everywhere (2: the 4^3 array of roots of Sec. 4)
     bool finalized = false;
 };
 
@@ -307,9 +308,11 @@ int64_t collapse_partition(Builder& B, int32_t p) {
     return B.P[p].ckey;
 }
 
-// Breadth-first walk; writes records/leaves when the output pointers are given.
+// Breadth-first walk; writes records/leaves when the output pointers are given. Cells above
+// level root_levels are always records: a uniform one (tree -2) where the cell is a leaf.
 int bfs(Builder& B, int32_t* nodes, uint16_t* leaves, int64_t* n_rec, int64_t* n_leaf, int32_t* levels) {
     std::deque<std::pair<std::pair<int32_t, int32_t>, int32_t>> q;
+    std::vector<uint64_t> uniform;
     q.push_back({{-1, 0}, 0});
     int64_t next_rec = 1, nl = 0, ri = 0;
     int32_t maxl = 1;
@@ -318,9 +321,13 @@ int bfs(Builder& B, int32_t* nodes, uint16_t* leaves, int64_t* n_rec, int64_t* n
         q.pop_front();
         if (lev + 1 > maxl) maxl = lev + 1;
         for (int k = 0; k < 8; ++k) {
-            Slot s = resolve(B, h.first, h.second, k);
+            Slot s = h.first == -2 ? Slot{false, 0, 0, uniform[(size_t)h.second]} : resolve(B, h.first, h.second, k);
             int32_t out;
-            if (s.internal) {
+            if (!s.internal && lev + 1 < B.root_levels) {
+                out = (int32_t)next_rec++;
+                q.push_back({{-2, (int32_t)uniform.size()}, lev + 1});
+                uniform.push_back(s.key);
+            } else if (s.internal) {
                 if (next_rec >= 0x7FFFFFFF) return -1;
                 out = (int32_t)next_rec++;
                 q.push_back({{s.tree, s.rec}, lev + 1});
@@ -348,6 +355,14 @@ int bfs(Builder& B, int32_t* nodes, uint16_t* leaves, int64_t* n_rec, int64_t* n
 extern "C" {
 
 void synth_set_threads(int32_t n) { g_threads = n; }
+
+// Keep the top n levels refined everywhere (n = 2: a 4^3 array of roots); before finalize.
+int synth_tree_set_root_levels(void* h, int32_t n) {
+    Builder& B = *static_cast<Builder*>(h);
+    if (n < 1 || n >= B.D || B.finalized) return -1;
+    B.root_levels = n;
+    return 0;
+}
 
 // Partition cells holding more than n stamps are split when that is exact (default 512).
 void synth_set_split(int32_t n) { g_split = n > 0 ? n : 512; }

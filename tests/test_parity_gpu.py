@@ -130,6 +130,26 @@ def test_deep_embedding_mixed_passes_fp32_fails(level):
         assert max_err(img32, ref) > 1e-3   # canvas-coordinate FP32 drifts at this depth
 
 
+def test_root_array_canvas():
+    """A canvas whose top two levels are refined everywhere (the 4^3 array of octree roots of Sec. 4):
+    the mixed path against the oracle, and the same image as the merged canvas of the same strokes."""
+    rng = synth.Rng(170402724)
+    n = 400
+    U = rng.uniform(n * 8).reshape(n, 8)
+    c = 0.02 + 0.46 * U[:, 0:3]                      # strokes in one octant: the others are empty roots
+    r = (2.0 + 18.0 * U[:, 3]) / 256.0
+    q = np.c_[U[:, 4:7], 0.5 + 19.5 * U[:, 7]].astype(np.float32)
+    a = synth.stamp_canvas(8, 1.0, c, r, q)
+    b = synth.stamp_canvas(8, 1.0, c, r, q, root_levels=2)
+    assert np.all(b.nodes[0] > 0) and b.n_records > a.n_records
+    cams = synth.config_cameras(0, res_scale=0.5)
+    ref = oracle.render(b, cams)
+    img_b, _ = render(b, cams, key="root_array")
+    img_a, _ = render(a, cams, key="root_array_merged")
+    assert max_err(img_b, ref) <= TOL
+    assert max_err(img_a, img_b) <= TOL
+
+
 def test_c1_reduced_full_image():
     cv = config_canvas(1)
     cams = synth.config_cameras(1, res_scale=0.125)

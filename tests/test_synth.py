@@ -90,3 +90,27 @@ def test_camera_records():
     c4 = synth.config_cameras(4)
     assert c4.shape == (64,)
     assert np.all((c4["width"] >= 256) & (c4["width"] <= 2160))
+
+
+def test_root_array_keeps_top_levels():
+    """root_levels = 2: the 4^3 array of octree roots (Sec. 4) stored as records 1-8 everywhere; the dense
+    field is unchanged, and so is the image (coarsening invariance of the oracle)."""
+    import math
+
+    import oracle
+    rng = synth.Rng(7)
+    n = 30
+    U = rng.uniform(n * 8).reshape(n, 8)
+    c = np.r_[0.05 + 0.4 * U[:, 0:3], [[-0.3, -0.3, -0.3]]]
+    r = np.r_[(1.0 + 6.0 * U[:, 3]) / 64.0, [2.0]]   # the last stamp paints the whole canvas first ...
+    q = np.r_[np.c_[U[:, 4:7], 0.5 + 19.5 * U[:, 7]], [[0.3, 0.6, 0.9, 1.5]]].astype(np.float32)
+    order = np.r_[n, np.arange(n)]                    # ... so every level-1 cell is a painted leaf or refined
+    a = synth.stamp_canvas(6, 1.0, c[order], r[order], q[order])
+    b = synth.stamp_canvas(6, 1.0, c[order], r[order], q[order], root_levels=2)
+    assert np.all(b.nodes[0] == np.arange(1, 9))
+    assert np.any(a.nodes[0] < 0)                     # merged: some octants are single leaves
+    ga, gb = DenseGrid(a), DenseGrid(b)
+    assert np.array_equal(ga.sigma, gb.sigma) and np.array_equal(ga.rgb, gb.rgb)
+    cam = synth.cameras_array([synth.look_at_camera([1.2, 0.9, 1.7], [0, 0, 0], [0, 1, 0], math.tan(math.radians(30)),
+                                                    40, 30, 0, (0.1, 0.2, 0.3, 1))])
+    np.testing.assert_allclose(oracle.render(b, cam, t_min=0.0), oracle.render(a, cam, t_min=0.0), rtol=0, atol=1e-13)
