@@ -257,7 +257,9 @@ def main():
 
     cid = args.config
     opts = json.loads(args.opts) if args.opts else {}
+    t_host = time.perf_counter()
     canvas = synth.build_config(cid, n_fine=args.n_fine or None)
+    host_paint_s = time.perf_counter() - t_host
     cams = synth.config_cameras(cid, res_scale=args.res_scale)
     n_px = synth.total_pixels(cams)
     cx.upload_octree(canvas.nodes, canvas.leaves, canvas.depth, canvas.extent)
@@ -406,6 +408,18 @@ def main():
         # the oracle on one core (a smaller sample; the all-core figure above is the baseline)
         _, _, rate1, wall1, _, _ = oracle_rate(canvas, cams, max(2.0, args.cpu_seconds / 3), seed=54321, threads=1)
         line["cpu_baseline_1core"] = {"value": rate1, "unit": "Mrays/s", "cores": 1, "seconds": round(wall1, 1)}
+        # the device stamp painter on the same stamp table (replaces the uploaded canvas; last)
+        D_, E_, c_, r_, q_, _ = synth.config_stamps(cid, n_fine=args.n_fine or None)
+        cx.paint_spheres(D_, E_, c_[:8], r_[:8], q_[:8])   # warm-up (module load, allocator)
+        torch.cuda.synchronize()
+        t_dev = time.perf_counter()
+        nr_, nl_ = cx.paint_spheres(D_, E_, c_, r_, q_)
+        dev_paint_s = time.perf_counter() - t_dev
+        nodes_, leaves_ = cx.download_octree()
+        line["device_painter"] = {
+            "stamps": int(r_.shape[0]), "seconds": round(dev_paint_s, 3), "records": nr_, "leaves": nl_,
+            "host_painter_seconds": round(host_paint_s, 2), "host_threads": os.cpu_count(),
+            "identical_to_host_pools": bool(np.array_equal(nodes_, canvas.nodes) and np.array_equal(leaves_, canvas.leaves))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -160,6 +160,38 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
                          int64_t n_leaves, int32_t depth, double extent);
 
 /*
+ * Paint a canvas on the GPU and make it the current one (replaces canvox_upload_octree
+ * for canvases built from spherical brush stamps; Sec. 5.1-5.2). Stamp i (applied in
+ * order i = 0, 1, ...) is a sphere with centre centers[3i..3i+2] and radius radii[i]
+ * (canvas units, host FP64) and brush value rgba[4i..4i+3] (host FP32 R, G, B, extinction).
+ * Model: a stamp refines every cell it partially covers down to its target depth (the
+ * smallest k with extent 2^-k <= r/10, at most depth; eight children copy the parent),
+ * paints cells inside the sphere whole, paints partially covered cells at or below the
+ * target depth by their centre, and descends into cells already refined. Paint blends
+ * additively in FP32 (rgb' = B m + (1 - m) C, m = B_a / (B_a + C_a), a' = B_a + C_a).
+ * Leaves are then clamped (rgb to [0, 1], extinction to [0, 60000]), rounded to FP16,
+ * eight identical siblings merge bottom-up (the root stays), and the pools are written
+ * in the breadth-first layout of canvox_upload_octree. The result is bit-identical to
+ * painting the stamps one by one in that order. Synchronous; the previous canvas is
+ * freed first (also on failure). Temporary device memory: per tree level, the ordered
+ * stamp lists of the refined cells. n_records, n_leaves (optional) receive the pool
+ * sizes. Errors: INVALID_ARG (non-finite input, negative radius or extinction, bad
+ * depth/extent), OOM (device memory, or pools beyond int32 indices), CUDA.
+ */
+int canvox_paint_spheres(int32_t depth, double extent, const double* centers, const double* radii,
+                         const float* rgba, int64_t n, int64_t* n_records, int64_t* n_leaves);
+
+/* Sizes of the current canvas (any pointer may be NULL). */
+int canvox_canvas_info(int64_t* n_records, int64_t* n_leaves, int32_t* depth, double* extent);
+
+/*
+ * Copy the current canvas to host memory in the layout of canvox_upload_octree:
+ * node_pool int32[n_records][8], leaf_rgba uint16[n_leaves][4] (sizes from
+ * canvox_canvas_info). Synchronous.
+ */
+int canvox_download_octree(int32_t* node_pool, uint16_t* leaf_rgba);
+
+/*
  * Render n_views views into out_rgba_dev (device float32 RGBA, at least
  * max(out_offset_px + width * height) pixels, 16 bytes each), stream-ordered
  * on `stream` (a cudaStream_t; NULL = legacy default stream) with the default

@@ -23,6 +23,9 @@ from .canvox import (  # noqa: F401
     octree_hash,
     autotune,
     footprint,
+    paint_spheres,
+    canvas_info,
+    download_octree,
     probe_l2_gather,
     probe_fp64,
     default_opts,

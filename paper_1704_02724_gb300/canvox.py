@@ -101,6 +101,14 @@ def lib():
         L.canvox_probe_l2_gather.restype = ctypes.c_int
         L.canvox_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
         L.canvox_probe_fp64.restype = ctypes.c_int
+        L.canvox_paint_spheres.argtypes = [i32, ctypes.c_double, vp, vp, vp, i64, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]
+        L.canvox_paint_spheres.restype = ctypes.c_int
+        L.canvox_canvas_info.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+        L.canvox_canvas_info.restype = ctypes.c_int
+        L.canvox_download_octree.argtypes = [vp, vp]
+        L.canvox_download_octree.restype = ctypes.c_int
         L.canvox_last_error.argtypes = []
         L.canvox_last_error.restype = ctypes.c_char_p
         L.canvox_release.argtypes = []
@@ -224,6 +232,37 @@ def autotune(cams, stream=None):
     o = Opts()
     _check(lib().canvox_autotune(cams.ctypes.data, cams.shape[0], _stream_ptr(stream), ctypes.byref(o)))
     return _opts_to_dict(o)
+
+
+def paint_spheres(depth, extent, centers, radii, rgba):
+    """canvox_paint_spheres: build the canvas of these stamps on the GPU; returns (n_records, n_leaves)."""
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
+    r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    q = np.ascontiguousarray(rgba, dtype=np.float32).reshape(-1, 4)
+    n = r.shape[0]
+    if c.shape[0] != n or q.shape[0] != n:
+        raise ValueError("centers, radii and rgba must have one row per stamp")
+    nr, nl = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().canvox_paint_spheres(int(depth), float(extent), c.ctypes.data if n else None,
+                                      r.ctypes.data if n else None, q.ctypes.data if n else None, n,
+                                      ctypes.byref(nr), ctypes.byref(nl)))
+    return nr.value, nl.value
+
+
+def canvas_info():
+    """canvox_canvas_info: (n_records, n_leaves, depth, extent) of the current canvas."""
+    nr, nl, d, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+    _check(lib().canvox_canvas_info(ctypes.byref(nr), ctypes.byref(nl), ctypes.byref(d), ctypes.byref(e)))
+    return nr.value, nl.value, d.value, e.value
+
+
+def download_octree():
+    """canvox_download_octree: (node_pool int32 [n_records, 8], leaf_rgba uint16 [n_leaves, 4])."""
+    nr, nl, _, _ = canvas_info()
+    nodes = np.empty((nr, 8), dtype=np.int32)
+    leaves = np.empty((max(nl, 1), 4), dtype=np.uint16)
+    _check(lib().canvox_download_octree(nodes.ctypes.data, leaves.ctypes.data))
+    return nodes, leaves[:nl]
 
 
 def footprint(cams, stream=None):

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/canvox.h"
@@ -119,6 +120,10 @@ cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, in
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 cudaError_t probe_l2_gather(int64_t buffer_bytes, double* gbs);
 cudaError_t probe_fp64(double* gflops);
+cudaError_t paint_pools(int32_t depth, double extent, const double* centers, const double* radii, const float* rgba,
+                        int64_t n, int32_t** d_nodes, uint2** d_leaves, int64_t* n_rec, int64_t* n_leaf,
+                        std::vector<int64_t>* level_begin);
+cudaError_t scan_i64(int64_t* d, int64_t n, int64_t* total);
 cudaError_t footprint_finish(const int32_t* nodes, const int64_t* level_begin, int n_levels, uint32_t* rec_bits,
                              int64_t rec_words, const uint32_t* leaf_bits, int64_t leaf_words,
                              unsigned long long* d_count, int64_t* n_records, int64_t* n_leaves);

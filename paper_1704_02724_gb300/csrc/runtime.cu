@@ -339,6 +339,40 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
 
 bool same_opts(const canvox_render_opts& a, const canvox_render_opts& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
 
+int check_canvas_args(int32_t depth, double extent) {
+    if (depth < 1 || depth > kMaxDepth) return fail(CANVOX_ERR_INVALID_ARG, "depth %d not in 1..30", depth);
+    if (!(extent > 0.0) || !std::isfinite(extent)) return fail(CANVOX_ERR_INVALID_ARG, "extent must be finite and > 0");
+    int ex;
+    const double m = std::frexp(extent, &ex);  // m in [0.5, 1)
+    const double scaled = std::ldexp(m, 23);  // integer iff at most 23 significant bits
+    if (scaled != std::floor(scaled))
+        return fail(CANVOX_ERR_INVALID_ARG, "extent %.17g has more than 23 significant bits", extent);
+    return CANVOX_OK;
+}
+
+// Wait for every render, then free the current canvas (pools and links).
+int drop_canvas() {
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    drop_graphs();
+    if (g.d_nodes) cudaFree(g.d_nodes);
+    if (g.d_leaves) cudaFree(g.d_leaves);
+    if (g.d_ropes) cudaFree(g.d_ropes);
+    g.d_nodes = nullptr;
+    g.d_leaves = nullptr;
+    g.d_ropes = nullptr;
+    g.uploaded = false;
+    return CANVOX_OK;
+}
+
+// Neighbour links of the current pools, one launch per level (parents first).
+int build_links() {
+    CK(cudaMalloc(&g.d_ropes, sizeof(uint2) * 6 * (size_t)g.n_rec), "cudaMalloc(ropes)");
+    for (size_t l = 0; l + 1 < g.level_begin.size(); ++l)
+        CK(launch_rope_level(g.d_nodes, g.d_ropes, g.level_begin[l], g.level_begin[l + 1], (int)l, 0), "rope kernel launch");
+    CK(cudaDeviceSynchronize(), "rope build");
+    return CANVOX_OK;
+}
+
 }  // namespace
 
 namespace canvox {
@@ -367,15 +401,8 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
         return fail(CANVOX_ERR_INVALID_ARG, "null pool or bad count");
     if (n_records > 0x7FFFFFFFll || n_leaves > 0x7FFFFFFFll)
         return fail(CANVOX_ERR_INVALID_ARG, "pool larger than int32 indices");
-    if (depth < 1 || depth > kMaxDepth) return fail(CANVOX_ERR_INVALID_ARG, "depth %d not in 1..30", depth);
-    if (!(extent > 0.0) || !std::isfinite(extent)) return fail(CANVOX_ERR_INVALID_ARG, "extent must be finite and > 0");
-    {
-        int ex;
-        const double m = std::frexp(extent, &ex);  // m in [0.5, 1)
-        const double scaled = std::ldexp(m, 23);  // integer iff at most 23 significant bits
-        if (scaled != std::floor(scaled))
-            return fail(CANVOX_ERR_INVALID_ARG, "extent %.17g has more than 23 significant bits", extent);
-    }
+    int rc = check_canvas_args(depth, extent);
+    if (rc) return rc;
     // validation: breadth-first numbering of records and leaves, depth bound, finite FP16 values
     std::vector<uint8_t> level((size_t)n_records, 0);
     int64_t next_rec = 1, next_leaf = 0;
@@ -415,18 +442,10 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
                                  ((unsigned long long)q[2] << 32) | ((unsigned long long)q[3] << 48);
         hh += elem_hash(2ull, (unsigned long long)i, val);
     }
-    int rc = ensure_device();
+    rc = ensure_device();
     if (rc) return rc;
     // replace the device copy
-    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
-    drop_graphs();
-    if (g.d_nodes) cudaFree(g.d_nodes);
-    if (g.d_leaves) cudaFree(g.d_leaves);
-    if (g.d_ropes) cudaFree(g.d_ropes);
-    g.d_nodes = nullptr;
-    g.d_leaves = nullptr;
-    g.d_ropes = nullptr;
-    g.uploaded = false;
+    if ((rc = drop_canvas())) return rc;
     CK(cudaMalloc(&g.d_nodes, sizeof(int32_t) * 8 * (size_t)n_records), "cudaMalloc(nodes)");
     CK(cudaMalloc(&g.d_leaves, sizeof(uint2) * (size_t)(n_leaves > 0 ? n_leaves : 1)), "cudaMalloc(leaves)");
     CK(cudaMemcpy(g.d_nodes, node_pool, sizeof(int32_t) * 8 * (size_t)n_records, cudaMemcpyHostToDevice), "cudaMemcpy(nodes)");
@@ -443,22 +462,78 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     unsigned long long dh = 0;
     CK(cudaMemcpy(&dh, g.d_hash, sizeof(dh), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
     if (dh != hh) return fail(CANVOX_ERR_CUDA, "device copy hash %016llx differs from host %016llx", dh, hh);
-    // neighbour links, level by level (breadth-first order keeps each level contiguous)
-    CK(cudaMalloc(&g.d_ropes, sizeof(uint2) * 6 * (size_t)n_records), "cudaMalloc(ropes)");
+    // records of each level (breadth-first order keeps each level contiguous)
     g.level_begin.assign(1, 0);
-    {
-        int64_t lo = 0;
-        while (lo < n_records) {
-            int64_t hi = lo;
-            const int lev = level[(size_t)lo];
-            while (hi < n_records && level[(size_t)hi] == lev) ++hi;
-            CK(launch_rope_level(g.d_nodes, g.d_ropes, lo, hi, lev, 0), "rope kernel launch");
-            g.level_begin.push_back(hi);
-            lo = hi;
-        }
-        CK(cudaDeviceSynchronize(), "rope build");
+    for (int64_t lo = 0; lo < n_records;) {
+        int64_t hi = lo;
+        while (hi < n_records && level[(size_t)hi] == level[(size_t)lo]) ++hi;
+        g.level_begin.push_back(hi);
+        lo = hi;
     }
+    if ((rc = build_links())) return rc;
     g.uploaded = true;
+    return CANVOX_OK;
+}
+
+int canvox_paint_spheres(int32_t depth, double extent, const double* centers, const double* radii, const float* rgba,
+                         int64_t n, int64_t* n_records, int64_t* n_leaves) {
+    g_err.clear();
+    if (n < 0 || (n > 0 && (!centers || !radii || !rgba)) || n >= 0x7FFFFFFFll)
+        return fail(CANVOX_ERR_INVALID_ARG, "null stamp arrays or bad count");
+    int rc = check_canvas_args(depth, extent);
+    if (rc) return rc;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(centers[3 * i]) || !std::isfinite(centers[3 * i + 1]) || !std::isfinite(centers[3 * i + 2]) ||
+            !std::isfinite(radii[i]) || radii[i] < 0.0)
+            return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: non-finite centre or bad radius", (long long)i);
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(rgba[4 * i + c])) return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: non-finite colour", (long long)i);
+        if (rgba[4 * i + 3] < 0.0f) return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: negative extinction", (long long)i);
+    }
+    if ((rc = ensure_device())) return rc;
+    if ((rc = drop_canvas())) return rc;
+    int32_t* nodes = nullptr;
+    uint2* leaves = nullptr;
+    int64_t nr = 0, nl = 0;
+    std::vector<int64_t> lb;
+    CK(paint_pools(depth, extent, centers, radii, rgba, n, &nodes, &leaves, &nr, &nl, &lb), "device painter");
+    g.d_nodes = nodes;
+    g.d_leaves = leaves;
+    if (nr > 0x7FFFFFFFll || nl > 0x7FFFFFFFll) return fail(CANVOX_ERR_OOM, "painted canvas exceeds int32 pool indices");
+    g.n_rec = nr;
+    g.n_leaf = nl;
+    g.depth = depth;
+    g.extent = extent;
+    g.level_begin = lb;
+    // no host copy exists: the device hash stands for both
+    CK(cudaMemset(g.d_hash, 0, sizeof(unsigned long long)), "cudaMemset(hash)");
+    CK(launch_hash(device_tree(), g.d_hash, 0), "hash kernel launch");
+    CK(cudaMemcpy(&g.host_hash, g.d_hash, sizeof(unsigned long long), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
+    if ((rc = build_links())) return rc;
+    g.uploaded = true;
+    if (n_records) *n_records = nr;
+    if (n_leaves) *n_leaves = nl;
+    return CANVOX_OK;
+}
+
+int canvox_canvas_info(int64_t* n_records, int64_t* n_leaves, int32_t* depth, double* extent) {
+    g_err.clear();
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    if (n_records) *n_records = g.n_rec;
+    if (n_leaves) *n_leaves = g.n_leaf;
+    if (depth) *depth = g.depth;
+    if (extent) *extent = g.extent;
+    return CANVOX_OK;
+}
+
+int canvox_download_octree(int32_t* node_pool, uint16_t* leaf_rgba) {
+    g_err.clear();
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    if (!node_pool || (g.n_leaf > 0 && !leaf_rgba)) return fail(CANVOX_ERR_INVALID_ARG, "null output");
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    CK(cudaMemcpy(node_pool, g.d_nodes, sizeof(int32_t) * 8 * (size_t)g.n_rec, cudaMemcpyDeviceToHost), "cudaMemcpy(nodes)");
+    if (g.n_leaf > 0)
+        CK(cudaMemcpy(leaf_rgba, g.d_leaves, sizeof(uint2) * (size_t)g.n_leaf, cudaMemcpyDeviceToHost), "cudaMemcpy(leaves)");
     return CANVOX_OK;
 }
 

@@ -179,4 +179,4 @@ def total_pixels(cams):
     return int(np.max(cams["out_offset_px"] + cams["width"].astype(np.int64) * cams["height"].astype(np.int64)))
 
 
-from .configs import CONFIGS, build_config, config_cameras  # noqa: E402,F401
+from .configs import CONFIGS, build_config, config_cameras, config_stamps  # noqa: E402,F401

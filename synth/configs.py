@@ -108,8 +108,8 @@ def _deep_stamps(rng, E, D, n_bg, n_fine, r_fine_min):
     return centers, radii, rgba, rooms
 
 
-def build_config(cid, n_fine=None):
-    """Build the canvas of a config. n_fine overrides the fine stamp count (c2-c4) for reduced variants."""
+def config_stamps(cid, n_fine=None):
+    """The stamp table of a config: (depth, extent, centres [n,3], radii [n], rgba [n,4] FP32, rooms or None)."""
     cfg = CONFIGS[cid]
     rng = Rng(SEED_BASE + cid)
     E, D = cfg["extent"], cfg["depth"]
@@ -125,6 +125,14 @@ def build_config(cid, n_fine=None):
         c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 100_000, E / 2.0 ** D)
     else:
         raise KeyError(cid)
+    return D, E, np.ascontiguousarray(c, dtype=np.float64), np.ascontiguousarray(r, dtype=np.float64), \
+        np.ascontiguousarray(q, dtype=np.float32), rooms
+
+
+def build_config(cid, n_fine=None):
+    """Build the canvas of a config. n_fine overrides the fine stamp count (c2-c4) for reduced variants."""
+    cfg = CONFIGS[cid]
+    D, E, c, r, q, rooms = config_stamps(cid, n_fine)
     cv = stamp_canvas(D, E, c, r, q)
     cv.info["config"] = cfg["name"]
     if rooms is not None:

@@ -1,0 +1,75 @@
+"""The device-side stamp painter (Sec. 5.1-5.2 on the GPU) against the host painter of the input
+generator: the pools must be identical, byte for byte, and so must the renders."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1704_02724_gb300 as cx
+import synth
+from gpu_util import _uploaded, render
+
+pytestmark = pytest.mark.gpu
+
+
+def _paint_and_compare(D, E, c, r, q):
+    ref = synth.stamp_canvas(D, E, c, r, q)
+    _uploaded["key"] = None                      # the painter replaces the uploaded canvas
+    nr, nl = cx.paint_spheres(D, E, c, r, q)
+    assert (nr, nl) == (ref.n_records, ref.n_leaves)
+    nodes, leaves = cx.download_octree()
+    np.testing.assert_array_equal(nodes, ref.nodes)
+    np.testing.assert_array_equal(leaves, ref.leaves)
+    h, d = cx.octree_hash()
+    assert h == d
+    return ref
+
+
+def test_paint_c0_identical_pools_and_image():
+    D, E, c, r, q, _ = synth.config_stamps(0)
+    ref = _paint_and_compare(D, E, c, r, q)
+    cams = synth.config_cameras(0)
+    n = synth.total_pixels(cams)
+    import torch
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    cx.render(cams, out)
+    torch.cuda.synchronize()
+    painted = out.cpu().numpy()
+    img, _ = render(ref, cams, key="c0_host_painted")
+    np.testing.assert_array_equal(painted, img.astype(np.float32))
+
+
+@pytest.mark.parametrize("seed,D", [(1, 3), (2, 5), (3, 7), (4, 9), (5, 12), (6, 20)])
+def test_paint_random_stamps(seed, D):
+    """Overlapping stamps of every size: whole-canvas and outside stamps, radii down to below the finest cell,
+    repeated stamps (blend order), zero extinction and zero radius."""
+    rng = np.random.default_rng(seed)
+    E = [1.0, 3.0, 1000.0, 40000.0][seed % 4]
+    n = 300
+    c = rng.uniform(-0.6, 0.6, (n, 3)) * E
+    r = E * np.exp(rng.uniform(math.log(2.0 ** -(D + 1)), math.log(0.7), n))
+    q = np.c_[rng.uniform(0, 1, (n, 3)), rng.uniform(0, 30, n)].astype(np.float32)
+    c[:20] = c[20:40]                      # the same spheres again, other colours
+    r[:20] = r[20:40]
+    q[5, 3] = 0.0
+    r[6] = 0.0
+    c[7] = (0.0, 0.0, 0.0)
+    r[7] = 2.0 * E                         # covers the whole canvas
+    c[8] = (5.0 * E, 0.0, 0.0)             # outside
+    _paint_and_compare(D, E, c, r, q)
+
+
+def test_paint_empty_and_deep_reduced_c2():
+    _paint_and_compare(4, 1.0, np.zeros((0, 3)), np.zeros(0), np.zeros((0, 4), np.float32))
+    D, E, c, r, q, _ = synth.config_stamps(2, n_fine=4000)
+    _paint_and_compare(D, E, c, r, q)
+
+
+def test_paint_rejects_bad_input():
+    with pytest.raises(cx.CanvoxError):
+        cx.paint_spheres(8, 1.0, [[0, 0, 0]], [-1.0], [[1, 1, 1, 1]])
+    with pytest.raises(cx.CanvoxError):
+        cx.paint_spheres(8, 1.0, [[np.nan, 0, 0]], [0.1], [[1, 1, 1, 1]])
+    with pytest.raises(cx.CanvoxError):
+        cx.paint_spheres(31, 1.0, [[0, 0, 0]], [0.1], [[1, 1, 1, 1]])
+    _uploaded["key"] = None
