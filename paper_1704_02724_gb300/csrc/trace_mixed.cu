@@ -112,11 +112,11 @@ struct Cold {
     double inv64[3], nod64[3];  // t(P) = P inv + nod; axis with d = 0: inv = 0, nod = o
     double tf;                  // FP64 ray parameter at the frame origin
     double invS;                // 1 / frame size
-    int64_t pix;                // output pixel
+    uint32_t pix;               // output pixel within the view (below width * height < 2^31)
     int32_t view;
     uint32_t n_rays, n_steps, n_f64, n_rebase;
-    uint32_t pad;
 };
+static_assert(sizeof(Cold) == 88, "per-lane shared record: 88 bytes keeps four blocks within the 132 KB carve-out");
 
 struct Ray {
     Cold* k;
@@ -205,8 +205,9 @@ __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
     o.y = ACC(r, 1) + r.T * V.bg[1];
     o.z = ACC(r, 2) + r.T * V.bg[2];
     o.w = 1.0f - r.T;
-    P.out[r.k->pix] = o;
-    if (P.step_count) P.step_count[r.k->pix] = r.steps;
+    const int64_t pix = V.out_offset + (int64_t)r.k->pix;
+    P.out[pix] = o;
+    if (P.step_count) P.step_count[pix] = r.steps;
     r.k->n_rays += 1;
     r.k->n_steps += (uint32_t)r.steps;
 }
@@ -256,7 +257,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     const int j = (int)ty * (32 >> wl) + (lane >> wl);
     if (i >= V.width || j >= V.height) return false;  // padding lane of a ragged tile
     r.k->view = lo;
-    r.k->pix = V.out_offset + (int64_t)j * V.width + i;
+    r.k->pix = (uint32_t)j * (uint32_t)V.width + (uint32_t)i;
     ACC(r, 0) = ACC(r, 1) = ACC(r, 2) = ACC(r, 3) = ACC(r, 4) = ACC(r, 5) = 0.0f;
     ACC(r, 6) = ACC(r, 7) = 0.0f;
     r.T = 1.0f;
