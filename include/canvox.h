@@ -49,7 +49,7 @@ extern "C" {
  *       exactly orthonormal: the library orthonormalises them by Gram-Schmidt
  *       starting from forward, then up, then right.
  *   tan_half_fov_y : tangent of half the vertical field of view (> 0).
- *   width, height  : image size in pixels (>= 1 each).
+ *   width, height  : image size in pixels (>= 1 each, width * height < 2^31).
  *   out_offset_px  : index of this view's pixel (0,0) in the output image;
  *       pixel (i, j) (column i, row j from the top) is written at
  *       out_offset_px + j * width + i. Views must not overlap.

@@ -23,7 +23,9 @@
 //     covered and has its centre inside s.
 // Each level keeps, per refined cell, the ordered list of stamps that still
 // descend (undecided) or already paint its whole subtree (painted); a child
-// classifies its parent's list against its own box. Geometry is FP64 with the
+// (one warp) classifies its parent's list against its own box, 32 entries at
+// a time, so a cell around a room with tens of thousands of stamps is split
+// across lanes instead of one thread. Geometry is FP64 with the
 // same operations and order as the host painter, so the pools are identical.
 #include <cmath>
 #include <cstring>
@@ -118,11 +120,40 @@ __device__ __forceinline__ int classify(const StampDev& S, int32_t s, const doub
     return d2 < r2 ? kPaint : kDrop;
 }
 
-// One thread per child: its first refining stamp, then either the leaf key or the size of its list.
-__global__ void expand_count(LevelIn L, StampDev S, int32_t depth, double extent, double half, int32_t* firstref,
-                             uint64_t* slot, int64_t* count, int64_t* is_int) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8 * L.n) return;
+// One warp per child; lanes take the parent's list 32 entries at a time, in order.
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+constexpr int kWarpsPerBlock = 4;
+
+// First stamp of the list that refines the child (partially covers it, target depth below it).
+__device__ __forceinline__ int32_t first_refining(const LevelIn& L, const StampDev& S, int64_t b, int64_t e, int lc,
+                                                  int32_t depth, const double lo[3], double h, int lane) {
+    if (lc >= depth) return 0x7FFFFFFF;
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t q = base + lane;
+        int32_t v = -1;
+        bool qual = false;
+        if (q < e) {
+            v = L.ent[q];
+            if (v >= 0 && S.kt[v] > lc) {
+                double dmin2, dmax2;
+                box_dist2(S.c + 3 * (int64_t)v, lo, h, dmin2, dmax2);
+                const double r2 = S.r2[v];
+                qual = dmin2 < r2 && dmax2 > r2;
+            }
+        }
+        const unsigned m = __ballot_sync(kFullMask, qual);
+        if (m) return __shfl_sync(kFullMask, v, __ffs(m) - 1);  // entries are in stamp order
+    }
+    return 0x7FFFFFFF;
+}
+
+// The child's first refining stamp, then either its leaf key or the size of its list.
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_count(LevelIn L, StampDev S, int32_t depth, double extent,
+                                                                    double half, int32_t* firstref, uint64_t* slot,
+                                                                    int64_t* count, int64_t* is_int) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= 8 * L.n) return;  // warp-uniform
     const int64_t i = t >> 3;
     const int k = (int)(t & 7);
     uint32_t cc[3];
@@ -130,50 +161,61 @@ __global__ void expand_count(LevelIn L, StampDev S, int32_t depth, double extent
     child_box(L, i, k, extent, half, cc, lo, h);
     const int lc = L.level + 1;
     const int64_t b = L.off[i], e = L.off[i + 1];
-    int32_t fr = 0x7FFFFFFF;
-    if (lc < depth) {
-        for (int64_t q = b; q < e; ++q) {
-            const int32_t v = L.ent[q];
-            if (v < 0 || S.kt[v] <= lc) continue;
-            double dmin2, dmax2;
-            box_dist2(S.c + 3 * (int64_t)v, lo, h, dmin2, dmax2);
-            const double r2 = S.r2[v];
-            if (dmin2 < r2 && dmax2 > r2) {
-                fr = v;  // entries are in stamp order: the first one is the minimum
-                break;
-            }
-        }
-    }
-    firstref[t] = fr;
+    const int32_t fr = first_refining(L, S, b, e, lc, depth, lo, h, lane);
     if (fr != 0x7FFFFFFF) {
         int64_t n = 0;
-        for (int64_t q = b; q < e; ++q) {
-            const int32_t v = L.ent[q];
-            if (v < 0 || classify(S, v, lo, h, fr <= v) != kDrop) ++n;
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t q = base + lane;
+            bool keep = false;
+            if (q < e) {
+                const int32_t v = L.ent[q];
+                keep = v < 0 || classify(S, v, lo, h, fr <= v) != kDrop;
+            }
+            n += __popc(__ballot_sync(kFullMask, keep));
         }
-        count[t] = n;
-        is_int[t] = 1;
-        slot[t] = kInternal;
+        if (lane == 0) {
+            firstref[t] = fr;
+            count[t] = n;
+            is_int[t] = 1;
+            slot[t] = kInternal;
+        }
     } else {
+        // a leaf: blend the stamps that paint it, in stamp order (every lane folds the same sequence)
         float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t q = b; q < e; ++q) {
-            const int32_t v = L.ent[q];
-            const int32_t s = v < 0 ? ~v : v;
-            if (v < 0 || classify(S, v, lo, h, false) == kPaint) blend(val, S.rgba[s]);
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t q = base + lane;
+            bool paint = false;
+            int32_t s = 0;
+            if (q < e) {
+                const int32_t v = L.ent[q];
+                s = v < 0 ? ~v : v;
+                paint = v < 0 || classify(S, v, lo, h, false) == kPaint;
+            }
+            unsigned m = __ballot_sync(kFullMask, paint);
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                blend(val, S.rgba[__shfl_sync(kFullMask, s, j)]);
+            }
         }
-        count[t] = 0;
-        is_int[t] = 0;
-        slot[t] = leaf_key(val);
+        if (lane == 0) {
+            firstref[t] = fr;
+            count[t] = 0;
+            is_int[t] = 0;
+            slot[t] = leaf_key(val);
+        }
     }
 }
 
 // Refined children: coordinates, list offsets and entries at the next level, slot = index there.
-__global__ void expand_write(LevelIn L, StampDev S, double extent, double half, const int32_t* firstref, uint64_t* slot,
-                             const int64_t* ent_off, const int64_t* next_idx, uint32_t* ncoord, int64_t* noff,
-                             int32_t* nent) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_write(LevelIn L, StampDev S, double extent, double half,
+                                                                    const int32_t* firstref, uint64_t* slot,
+                                                                    const int64_t* ent_off, const int64_t* next_idx,
+                                                                    uint32_t* ncoord, int64_t* noff, int32_t* nent) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (t >= 8 * L.n) return;
-    if (slot[t] != kInternal) return;
+    if (slot[t] != kInternal) return;  // warp-uniform
     const int64_t i = t >> 3;
     const int k = (int)(t & 7);
     uint32_t cc[3];
@@ -181,21 +223,34 @@ __global__ void expand_write(LevelIn L, StampDev S, double extent, double half, 
     child_box(L, i, k, extent, half, cc, lo, h);
     const int32_t fr = firstref[t];
     const int64_t j = next_idx[t];
-    slot[t] = kInternal | (uint64_t)j;
-    ncoord[3 * j] = cc[0];
-    ncoord[3 * j + 1] = cc[1];
-    ncoord[3 * j + 2] = cc[2];
     int64_t w = ent_off[t];
-    noff[j] = w;
-    for (int64_t q = L.off[i]; q < L.off[i + 1]; ++q) {
-        const int32_t v = L.ent[q];
-        if (v < 0) {
-            nent[w++] = v;
-            continue;
+    __syncwarp();
+    if (lane == 0) {
+        slot[t] = kInternal | (uint64_t)j;
+        ncoord[3 * j] = cc[0];
+        ncoord[3 * j + 1] = cc[1];
+        ncoord[3 * j + 2] = cc[2];
+        noff[j] = w;
+    }
+    const int64_t b = L.off[i], e = L.off[i + 1];
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t q = base + lane;
+        int32_t out = 0;
+        bool keep = false;
+        if (q < e) {
+            const int32_t v = L.ent[q];
+            if (v < 0) {
+                out = v;
+                keep = true;
+            } else {
+                const int c = classify(S, v, lo, h, fr <= v);
+                keep = c != kDrop;
+                out = c == kPaint ? ~v : v;
+            }
         }
-        const int c = classify(S, v, lo, h, fr <= v);
-        if (c == kPaint) nent[w++] = ~v;
-        else if (c == kKeep) nent[w++] = v;
+        const unsigned m = __ballot_sync(kFullMask, keep);
+        if (keep) nent[w + __popc(m & ((1u << lane) - 1u))] = out;
+        w += __popc(m);
     }
 }
 
@@ -435,7 +490,8 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* h_centers, c
         PCK(buf.alloc(&slot, nch));
         PCK(buf.alloc(&cnt, nch));
         PCK(buf.alloc(&isint, nch));
-        expand_count<<<blocks_for(nch, 128), 128>>>(L, S, depth, extent, half, fr, slot, cnt, isint);
+        expand_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr, slot, cnt,
+                                                                                   isint);
         PCK(cudaGetLastError());
         int64_t n_ent = 0, n_next = 0;
         PCK(scan_i64(cnt, nch, &n_ent));
@@ -455,7 +511,8 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* h_centers, c
         PCK(buf.alloc(&noff, n_next + 1));
         PCK(buf.alloc(&nent, n_ent));
         PCK(cudaMemcpy(noff + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
-        expand_write<<<blocks_for(nch, 128), 128>>>(L, S, extent, half, fr, slot, cnt, isint, ncoord, noff, nent);
+        expand_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot, cnt, isint,
+                                                                                   ncoord, noff, nent);
         PCK(cudaGetLastError());
         PCK(cudaDeviceSynchronize());
         buf.release(fr);

@@ -187,6 +187,8 @@ int setup_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t
             return fail(CANVOX_ERR_INVALID_ARG, "camera %d: bad size, field of view, offset or non-finite vector", v);
         for (int a = 0; a < 4; ++a)
             if (!std::isfinite(c.background[a])) return fail(CANVOX_ERR_INVALID_ARG, "camera %d: non-finite background", v);
+        if ((int64_t)c.width * c.height > 0x7FFFFFFFll)
+            return fail(CANVOX_ERR_INVALID_ARG, "camera %d: more than 2^31 - 1 pixels", v);
         View& V = out[v];
         std::memset(&V, 0, sizeof(V));
         double n0 = std::sqrt(dot3(c.forward, c.forward));

@@ -262,6 +262,11 @@ def test_empty_canvas_zero_views_and_bad_cameras():
     bad[1]["tan_half_fov_y"] = math.nan
     with pytest.raises(cx.CanvoxError):
         cx.render(bad, out)
+    bad = cams.copy()
+    bad[0]["width"], bad[0]["height"] = 65536, 32768   # 2^31 pixels: beyond the per-view limit
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.render(bad, out)
+    assert e.value.code == canvox.ERR_INVALID_ARG
 
 
 def test_bad_upload_keeps_previous_canvas():
