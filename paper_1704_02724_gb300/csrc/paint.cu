@@ -22,10 +22,11 @@
 //     first cell s does not descend through lies inside s, or is partially
 //     covered and has its centre inside s.
 // Each level keeps, per refined cell, the ordered list of stamps that still
-// descend (undecided) or already paint its whole subtree (painted); a child
-// (one warp) classifies its parent's list against its own box, 32 entries at
-// a time, so a cell around a room with tens of thousands of stamps is split
-// across lanes instead of one thread. Geometry is FP64 with the
+// descend (undecided) or already paint its whole subtree (painted); one warp
+// per refined cell classifies that list against its eight children, 32
+// entries at a time (a cell around a room holds tens of thousands of stamps),
+// with each stamp's distances to the cell's three planes per axis shared by
+// the children. Geometry is FP64 with the
 // same operations and order as the host painter, so the pools are identical.
 #include <cmath>
 #include <cstring>
@@ -92,114 +93,169 @@ struct LevelIn {
     const int32_t* ent;     // s: descends, ~s: paints the whole cell
 };
 
-// Box of child k of cell i at level l + 1.
-__device__ __forceinline__ void child_box(const LevelIn& L, int64_t i, int k, double extent, double half, uint32_t cc[3],
-                                          double lo[3], double& h) {
-    h = extent * __longlong_as_double((long long)(1023 - (L.level + 1)) << 52);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        cc[a] = 2u * L.coord[3 * i + a] + ((k >> a) & 1u);
-        lo[a] = fma((double)cc[a], h, -half);  // exact: a multiple of h inside the canvas
-    }
-}
-
 enum { kDrop = 0, kPaint = 1, kKeep = 2 };
 
-// Classify stamp s (undecided at the parent) for a child box; refined = child refined by the time s arrives.
-__device__ __forceinline__ int classify(const StampDev& S, int32_t s, const double lo[3], double h, bool refined) {
-    double dmin2, dmax2;
-    const double r2 = S.r2[s];
-    box_dist2(S.c + 3 * (int64_t)s, lo, h, dmin2, dmax2);
-    if (dmin2 >= r2) return kDrop;
-    if (dmax2 <= r2) return kPaint;
-    if (refined) return kKeep;
-    const double hh = 0.5 * h;
-    const double* c = S.c + 3 * (int64_t)s;
-    const double d2 = __dadd_rn(__dadd_rn(sq(__dsub_rn(__dadd_rn(lo[0], hh), c[0])), sq(__dsub_rn(__dadd_rn(lo[1], hh), c[1]))),
-                                sq(__dsub_rn(__dadd_rn(lo[2], hh), c[2])));
-    return d2 < r2 ? kPaint : kDrop;
-}
-
-// One warp per child; lanes take the parent's list 32 entries at a time, in order.
+// Lanes take a cell's stamp list 32 entries at a time, in order.
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kWarpsPerBlock = 4;
 
-// First stamp of the list that refines the child (partially covers it, target depth below it).
-__device__ __forceinline__ int32_t first_refining(const LevelIn& L, const StampDev& S, int64_t b, int64_t e, int lc,
-                                                  int32_t depth, const double lo[3], double h, int lane) {
-    if (lc >= depth) return 0x7FFFFFFF;
-    for (int64_t base = b; base < e; base += 32) {
-        const int64_t q = base + lane;
-        int32_t v = -1;
-        bool qual = false;
-        if (q < e) {
-            v = L.ent[q];
-            if (v >= 0 && S.kt[v] > lc) {
-                double dmin2, dmax2;
-                box_dist2(S.c + 3 * (int64_t)v, lo, h, dmin2, dmax2);
-                const double r2 = S.r2[v];
-                qual = dmin2 < r2 && dmax2 > r2;
-            }
-        }
-        const unsigned m = __ballot_sync(kFullMask, qual);
-        if (m) return __shfl_sync(kFullMask, v, __ffs(m) - 1);  // entries are in stamp order
+// One warp per refined cell, all eight children at once. Per axis a stamp's squared distances to the
+// cell's three planes (low, mid, high) serve both halves, so a child's box distances are sums of
+// per-axis terms already formed: (t0 + t1) + t2, the host painter's sums with its zero terms dropped,
+// which leaves them bit-identical (adding +0 is exact).
+struct ParentTerms {
+    double dmin[2][3], dmax[2][3];  // [bit][axis]
+    double cen[2][3];               // squared distance to the child centre's coordinate
+};
+
+__device__ __forceinline__ void parent_terms(const double* c, const double pl[3], const double pm[3], const double pu[3],
+                                             const double cl[3], const double cm[3], ParentTerms& T) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double A = sq(__dsub_rn(c[a], pl[a])), B = sq(__dsub_rn(c[a], pm[a])), C = sq(__dsub_rn(c[a], pu[a]));
+        T.dmin[0][a] = c[a] < pl[a] ? A : (c[a] > pm[a] ? B : 0.0);
+        T.dmin[1][a] = c[a] < pm[a] ? B : (c[a] > pu[a] ? C : 0.0);
+        T.dmax[0][a] = fmax(A, B);
+        T.dmax[1][a] = fmax(B, C);
+        T.cen[0][a] = sq(__dsub_rn(cl[a], c[a]));
+        T.cen[1][a] = sq(__dsub_rn(cm[a], c[a]));
     }
-    return 0x7FFFFFFF;
 }
 
-// The child's first refining stamp, then either its leaf key or the size of its list.
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_count(LevelIn L, StampDev S, int32_t depth, double extent,
-                                                                    double half, int32_t* firstref, uint64_t* slot,
-                                                                    int64_t* count, int64_t* is_int) {
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (t >= 8 * L.n) return;  // warp-uniform
-    const int64_t i = t >> 3;
-    const int k = (int)(t & 7);
-    uint32_t cc[3];
-    double lo[3], h;
-    child_box(L, i, k, extent, half, cc, lo, h);
+// Child k: kDrop / kPaint / kKeep for an undecided stamp with squared radius r2.
+__device__ __forceinline__ int classify_child(const ParentTerms& T, int k, double r2, bool refined) {
+    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+    const double dmin2 = __dadd_rn(__dadd_rn(T.dmin[b0][0], T.dmin[b1][1]), T.dmin[b2][2]);
+    if (dmin2 >= r2) return kDrop;
+    const double dmax2 = __dadd_rn(__dadd_rn(T.dmax[b0][0], T.dmax[b1][1]), T.dmax[b2][2]);
+    if (dmax2 <= r2) return kPaint;
+    if (refined) return kKeep;
+    const double d2 = __dadd_rn(__dadd_rn(T.cen[b0][0], T.cen[b1][1]), T.cen[b2][2]);
+    return d2 < r2 ? kPaint : kDrop;
+}
+
+__device__ __forceinline__ void parent_planes(const LevelIn& L, int64_t i, double extent, double half, double pl[3],
+                                              double pm[3], double pu[3], double cl[3], double cm[3]) {
+    const double H = extent * __longlong_as_double((long long)(1023 - L.level) << 52);
+    const double h = 0.5 * H, hh = 0.5 * h;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        pl[a] = fma((double)L.coord[3 * i + a], H, -half);  // exact: multiples of the cell size
+        pm[a] = __dadd_rn(pl[a], h);
+        pu[a] = __dadd_rn(pm[a], h);
+        cl[a] = __dadd_rn(pl[a], hh);
+        cm[a] = __dadd_rn(pm[a], hh);
+    }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(LevelIn L, StampDev S, int32_t depth,
+                                                                           double extent, double half, int32_t* firstref,
+                                                                           uint64_t* slot, int64_t* count, int64_t* is_int) {
+    __shared__ int32_t s_idx[kWarpsPerBlock][32];
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (i >= L.n) return;  // warp-uniform
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
     const int lc = L.level + 1;
     const int64_t b = L.off[i], e = L.off[i + 1];
-    const int32_t fr = first_refining(L, S, b, e, lc, depth, lo, h, lane);
-    if (fr != 0x7FFFFFFF) {
-        int64_t n = 0;
-        for (int64_t base = b; base < e; base += 32) {
+    // the first refining stamp of each child
+    int32_t fr[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fr[k] = 0x7FFFFFFF;
+    unsigned found = 0;
+    if (lc < depth) {
+        for (int64_t base = b; base < e && found != 0xFFu; base += 32) {
             const int64_t q = base + lane;
-            bool keep = false;
+            int32_t v = -1;
+            bool cand = false;
+            ParentTerms T;
+            double r2 = 0.0;
             if (q < e) {
-                const int32_t v = L.ent[q];
-                keep = v < 0 || classify(S, v, lo, h, fr <= v) != kDrop;
+                v = L.ent[q];
+                if (v >= 0 && S.kt[v] > lc) {
+                    cand = true;
+                    r2 = S.r2[v];
+                    parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                }
             }
-            n += __popc(__ballot_sync(kFullMask, keep));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                bool qual = false;
+                if (cand) {
+                    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+                    const double dmin2 = __dadd_rn(__dadd_rn(T.dmin[b0][0], T.dmin[b1][1]), T.dmin[b2][2]);
+                    const double dmax2 = __dadd_rn(__dadd_rn(T.dmax[b0][0], T.dmax[b1][1]), T.dmax[b2][2]);
+                    qual = dmin2 < r2 && dmax2 > r2;
+                }
+                const unsigned m = __ballot_sync(kFullMask, qual);
+                const int32_t first = __shfl_sync(kFullMask, v, m ? __ffs(m) - 1 : 0);
+                if (m && !((found >> k) & 1u)) {
+                    fr[k] = first;
+                    found |= 1u << k;
+                }
+            }
         }
-        if (lane == 0) {
-            firstref[t] = fr;
-            count[t] = n;
+    }
+    // counts of the refined children, blends of the leaf children (lane k folds child k)
+    int64_t n[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) n[k] = 0;
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t q = base + lane;
+        int32_t v = 0;
+        bool valid = false;
+        ParentTerms T;
+        double r2 = 0.0;
+        if (q < e) {
+            valid = true;
+            v = L.ent[q];
+            if (v >= 0) {
+                r2 = S.r2[v];
+                parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+            }
+        }
+        s_idx[wib][lane] = v < 0 ? ~v : v;
+        unsigned pmask = 0;  // lane k: the entries that paint leaf child k
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool internal = fr[k] != 0x7FFFFFFF;
+            int c = kDrop;
+            if (valid) c = v < 0 ? kPaint : classify_child(T, k, r2, internal && fr[k] <= v);
+            if (internal) {
+                n[k] += __popc(__ballot_sync(kFullMask, c != kDrop));
+            } else {
+                const unsigned m = __ballot_sync(kFullMask, c == kPaint);
+                if (lane == k) pmask = m;
+            }
+        }
+        __syncwarp();
+        if (lane < 8) {
+            while (pmask) {
+                const int j = __ffs(pmask) - 1;
+                pmask &= pmask - 1;
+                blend(val, S.rgba[s_idx[wib][j]]);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane < 8) {
+        int64_t nk = 0;
+        int32_t fk = 0x7FFFFFFF;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (lane == k) {
+                nk = n[k];
+                fk = fr[k];
+            }
+        const int64_t t = 8 * i + lane;
+        firstref[t] = fk;
+        if (fk != 0x7FFFFFFF) {
+            count[t] = nk;
             is_int[t] = 1;
             slot[t] = kInternal;
-        }
-    } else {
-        // a leaf: blend the stamps that paint it, in stamp order (every lane folds the same sequence)
-        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t base = b; base < e; base += 32) {
-            const int64_t q = base + lane;
-            bool paint = false;
-            int32_t s = 0;
-            if (q < e) {
-                const int32_t v = L.ent[q];
-                s = v < 0 ? ~v : v;
-                paint = v < 0 || classify(S, v, lo, h, false) == kPaint;
-            }
-            unsigned m = __ballot_sync(kFullMask, paint);
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                blend(val, S.rgba[__shfl_sync(kFullMask, s, j)]);
-            }
-        }
-        if (lane == 0) {
-            firstref[t] = fr;
+        } else {
             count[t] = 0;
             is_int[t] = 0;
             slot[t] = leaf_key(val);
@@ -207,50 +263,60 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_count(LevelIn L, S
     }
 }
 
-// Refined children: coordinates, list offsets and entries at the next level, slot = index there.
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_write(LevelIn L, StampDev S, double extent, double half,
-                                                                    const int32_t* firstref, uint64_t* slot,
-                                                                    const int64_t* ent_off, const int64_t* next_idx,
-                                                                    uint32_t* ncoord, int64_t* noff, int32_t* nent) {
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_write(LevelIn L, StampDev S, double extent,
+                                                                           double half, const int32_t* firstref,
+                                                                           uint64_t* slot, const int64_t* ent_off,
+                                                                           const int64_t* next_idx, uint32_t* ncoord,
+                                                                           int64_t* noff, int32_t* nent) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (t >= 8 * L.n) return;
-    if (slot[t] != kInternal) return;  // warp-uniform
-    const int64_t i = t >> 3;
-    const int k = (int)(t & 7);
-    uint32_t cc[3];
-    double lo[3], h;
-    child_box(L, i, k, extent, half, cc, lo, h);
-    const int32_t fr = firstref[t];
-    const int64_t j = next_idx[t];
-    int64_t w = ent_off[t];
-    __syncwarp();
-    if (lane == 0) {
-        slot[t] = kInternal | (uint64_t)j;
-        ncoord[3 * j] = cc[0];
-        ncoord[3 * j + 1] = cc[1];
-        ncoord[3 * j + 2] = cc[2];
-        noff[j] = w;
+    if (i >= L.n) return;
+    int32_t fr[8];
+    int64_t w[8];
+    unsigned internal = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        fr[k] = firstref[8 * i + k];
+        w[k] = ent_off[8 * i + k];
+        if (slot[8 * i + k] == kInternal) internal |= 1u << k;
     }
+    if (!internal) return;  // warp-uniform
+    __syncwarp();
+    if (lane < 8 && ((internal >> lane) & 1u)) {
+        const int64_t t = 8 * i + lane, j = next_idx[t];
+        slot[t] = kInternal | (uint64_t)j;
+        ncoord[3 * j] = 2u * L.coord[3 * i] + (lane & 1u);
+        ncoord[3 * j + 1] = 2u * L.coord[3 * i + 1] + ((lane >> 1) & 1u);
+        ncoord[3 * j + 2] = 2u * L.coord[3 * i + 2] + ((lane >> 2) & 1u);
+        noff[j] = ent_off[t];
+    }
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
     const int64_t b = L.off[i], e = L.off[i + 1];
     for (int64_t base = b; base < e; base += 32) {
         const int64_t q = base + lane;
-        int32_t out = 0;
-        bool keep = false;
+        int32_t v = 0;
+        bool valid = false;
+        ParentTerms T;
+        double r2 = 0.0;
         if (q < e) {
-            const int32_t v = L.ent[q];
-            if (v < 0) {
-                out = v;
-                keep = true;
-            } else {
-                const int c = classify(S, v, lo, h, fr <= v);
-                keep = c != kDrop;
-                out = c == kPaint ? ~v : v;
+            valid = true;
+            v = L.ent[q];
+            if (v >= 0) {
+                r2 = S.r2[v];
+                parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
             }
         }
-        const unsigned m = __ballot_sync(kFullMask, keep);
-        if (keep) nent[w + __popc(m & ((1u << lane) - 1u))] = out;
-        w += __popc(m);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (!((internal >> k) & 1u)) continue;  // warp-uniform
+            int c = kDrop;
+            if (valid) c = v < 0 ? kPaint : classify_child(T, k, r2, fr[k] <= v);
+            const bool keep = c != kDrop;
+            const unsigned m = __ballot_sync(kFullMask, keep);
+            if (keep) nent[w[k] + __popc(m & ((1u << lane) - 1u))] = (v < 0 || c == kKeep) ? v : ~v;
+            w[k] += __popc(m);
+        }
     }
 }
 
@@ -490,8 +556,8 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* h_centers, c
         PCK(buf.alloc(&slot, nch));
         PCK(buf.alloc(&cnt, nch));
         PCK(buf.alloc(&isint, nch));
-        expand_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr, slot, cnt,
-                                                                                   isint);
+        expand_parent_count<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr, slot,
+                                                                                       cnt, isint);
         PCK(cudaGetLastError());
         int64_t n_ent = 0, n_next = 0;
         PCK(scan_i64(cnt, nch, &n_ent));
@@ -511,8 +577,8 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* h_centers, c
         PCK(buf.alloc(&noff, n_next + 1));
         PCK(buf.alloc(&nent, n_ent));
         PCK(cudaMemcpy(noff + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
-        expand_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot, cnt, isint,
-                                                                                   ncoord, noff, nent);
+        expand_parent_write<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot, cnt,
+                                                                                       isint, ncoord, noff, nent);
         PCK(cudaGetLastError());
         PCK(cudaDeviceSynchronize());
         buf.release(fr);

@@ -1,5 +1,5 @@
 // Measurement helpers: the denominators and the footprint the traversal is
-// judged against (the paper has no counterpart; it reports no profile).
+// compared with (the paper has no counterpart; it reports no profile).
 //
 //   canvox_probe_l2_gather : random 32-byte sector gathers from an L2-resident
 //                            buffer, the access pattern of the record and leaf

@@ -16,7 +16,7 @@
 //
 // Canonical pool layout (Sec. 4.1.1: index-based pools, eight children per
 // allocation unit). Record r has eight int32 slots, child k = x + 2y + 4z
-// (Sec. 4.1.1, "C(D1) and C(D1)+2" places the +2 step along y):
+// (Sec. 4.1.1: in its quadtree example the cell above the first child is at offset 2, so +2 is y):
 //   slot > 0  : index of the child's record (always > r, breadth-first order)
 //   slot == 0 : empty leaf (extinction 0)
 //   slot < 0  : leaf index -slot-1 into the leaf pool of 4 x FP16 (R,G,B,sigma)
