@@ -416,10 +416,21 @@ def main():
         nr_, nl_ = cx.paint_spheres(D_, E_, c_, r_, q_)
         dev_paint_s = time.perf_counter() - t_dev
         nodes_, leaves_ = cx.download_octree()
+        same_full = bool(np.array_equal(nodes_, canvas.nodes) and np.array_equal(leaves_, canvas.leaves))
+        # the editing path: the last 1,000 stamps appended to a canvas painted from the others
+        k_ = max(0, r_.shape[0] - 1000)
+        cx.paint_spheres(D_, E_, c_[:k_], r_[:k_], q_[:k_])
+        t_app = time.perf_counter()
+        cx.paint_append(c_[k_:], r_[k_:], q_[k_:])
+        app_s = time.perf_counter() - t_app
+        nodes_, leaves_ = cx.download_octree()
+        same_app = bool(np.array_equal(nodes_, canvas.nodes) and np.array_equal(leaves_, canvas.leaves))
         line["device_painter"] = {
             "stamps": int(r_.shape[0]), "seconds": round(dev_paint_s, 3), "records": nr_, "leaves": nl_,
             "host_painter_seconds": round(host_paint_s, 2), "host_threads": os.cpu_count(),
-            "identical_to_host_pools": bool(np.array_equal(nodes_, canvas.nodes) and np.array_equal(leaves_, canvas.leaves))}
+            "identical_to_host_pools": same_full and same_app,
+            "append_last_stamps": int(r_.shape[0] - k_), "append_seconds": round(app_s, 3),
+            "append_h2d_bytes": int((r_.shape[0] - k_) * 56)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

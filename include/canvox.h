@@ -181,6 +181,17 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
 int canvox_paint_spheres(int32_t depth, double extent, const double* centers, const double* radii,
                          const float* rgba, int64_t n, int64_t* n_records, int64_t* n_leaves);
 
+/*
+ * Add n stamps after those already painted and repaint (the editing path: only the new
+ * stamps, 56 bytes each, cross the bus; the painter keeps the stamp table of the current
+ * canvas in device memory). The result is the canvas canvox_paint_spheres would build
+ * from the whole table. Needs a current canvas made by canvox_paint_spheres or this call
+ * (CANVOX_ERR_NOT_UPLOADED otherwise, e.g. after canvox_upload_octree). Same arguments,
+ * errors and synchronisation as canvox_paint_spheres; on an argument error nothing changes.
+ */
+int canvox_paint_append(const double* centers, const double* radii, const float* rgba, int64_t n,
+                        int64_t* n_records, int64_t* n_leaves);
+
 /* Sizes of the current canvas (any pointer may be NULL). */
 int canvox_canvas_info(int64_t* n_records, int64_t* n_leaves, int32_t* depth, double* extent);
 

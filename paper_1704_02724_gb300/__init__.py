@@ -24,6 +24,7 @@ from .canvox import (  # noqa: F401
     autotune,
     footprint,
     paint_spheres,
+    paint_append,
     canvas_info,
     download_octree,
     probe_l2_gather,

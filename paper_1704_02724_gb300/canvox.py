@@ -104,6 +104,8 @@ def lib():
         L.canvox_paint_spheres.argtypes = [i32, ctypes.c_double, vp, vp, vp, i64, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]
         L.canvox_paint_spheres.restype = ctypes.c_int
+        L.canvox_paint_append.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.canvox_paint_append.restype = ctypes.c_int
         L.canvox_canvas_info.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.canvox_canvas_info.restype = ctypes.c_int
@@ -246,6 +248,20 @@ def paint_spheres(depth, extent, centers, radii, rgba):
     _check(lib().canvox_paint_spheres(int(depth), float(extent), c.ctypes.data if n else None,
                                       r.ctypes.data if n else None, q.ctypes.data if n else None, n,
                                       ctypes.byref(nr), ctypes.byref(nl)))
+    return nr.value, nl.value
+
+
+def paint_append(centers, radii, rgba):
+    """canvox_paint_append: add stamps to the painted canvas and repaint; returns (n_records, n_leaves)."""
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
+    r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    q = np.ascontiguousarray(rgba, dtype=np.float32).reshape(-1, 4)
+    n = r.shape[0]
+    if c.shape[0] != n or q.shape[0] != n:
+        raise ValueError("centers, radii and rgba must have one row per stamp")
+    nr, nl = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().canvox_paint_append(c.ctypes.data if n else None, r.ctypes.data if n else None,
+                                     q.ctypes.data if n else None, n, ctypes.byref(nr), ctypes.byref(nl)))
     return nr.value, nl.value
 
 

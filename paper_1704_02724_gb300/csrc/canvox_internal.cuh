@@ -120,7 +120,7 @@ cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, in
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 cudaError_t probe_l2_gather(int64_t buffer_bytes, double* gbs);
 cudaError_t probe_fp64(double* gflops);
-cudaError_t paint_pools(int32_t depth, double extent, const double* centers, const double* radii, const float* rgba,
+cudaError_t paint_pools(int32_t depth, double extent, const double* d_centers, const double* d_radii, const float4* d_rgba,
                         int64_t n, int32_t** d_nodes, uint2** d_leaves, int64_t* n_rec, int64_t* n_leaf,
                         std::vector<int64_t>* level_begin);
 cudaError_t scan_i64(int64_t* d, int64_t n, int64_t* total);

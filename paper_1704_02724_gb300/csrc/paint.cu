@@ -320,6 +320,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_write(Level
     }
 }
 
+// Squared radius and target depth of each stamp: the smallest k with extent 2^-k <= r/10, at most depth.
+__global__ void stamp_prep(const double* r, int64_t n, int32_t depth, double extent, double* r2, int32_t* kt) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double rs = r[s];
+    r2[s] = __dmul_rn(rs, rs);
+    const double tgt = __ddiv_rn(rs, 10.0);
+    int32_t k = 0;
+    double w = extent;
+    while (k < depth && w > tgt) {
+        w = __dmul_rn(w, 0.5);
+        ++k;
+    }
+    kt[s] = k;
+}
+
 // Stamps that touch the canvas, in order (the root's list).
 __global__ void root_flags(StampDev S, int64_t n, double extent, double half, int64_t* flag) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -482,37 +498,19 @@ unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
         if (e_ != cudaSuccess) return e_;            \
     } while (0)
 
-cudaError_t paint_pools(int32_t depth, double extent, const double* h_centers, const double* h_radii, const float* h_rgba,
+cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const double* d_r, const float4* d_rgba,
                         int64_t n, int32_t** d_nodes_out, uint2** d_leaves_out, int64_t* n_rec_out, int64_t* n_leaf_out,
                         std::vector<int64_t>* level_begin) {
     const double half = 0.5 * extent;
     DevBuf buf;
-    // stamps: centres, squared radii, target depths (host integer loop, as the host painter), colours
-    std::vector<double> r2((size_t)(n > 0 ? n : 1));
-    std::vector<int32_t> kt((size_t)(n > 0 ? n : 1));
-    for (int64_t i = 0; i < n; ++i) {
-        r2[(size_t)i] = h_radii[i] * h_radii[i];
-        int32_t k = 0;
-        double w = extent;
-        const double tgt = h_radii[i] / 10.0;
-        while (k < depth && w > tgt) {
-            w *= 0.5;
-            ++k;
-        }
-        kt[(size_t)i] = k;
-    }
-    double *d_c, *d_r2;
+    // squared radii and target depths (the host painter's integer loop, in the same FP64 operations)
+    double* d_r2;
     int32_t* d_kt;
-    float4* d_rgba;
-    PCK(buf.alloc(&d_c, 3 * n));
     PCK(buf.alloc(&d_r2, n));
     PCK(buf.alloc(&d_kt, n));
-    PCK(buf.alloc(&d_rgba, n));
     if (n > 0) {
-        PCK(cudaMemcpy(d_c, h_centers, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice));
-        PCK(cudaMemcpy(d_r2, r2.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
-        PCK(cudaMemcpy(d_kt, kt.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
-        PCK(cudaMemcpy(d_rgba, h_rgba, sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice));
+        stamp_prep<<<blocks_for(n, 256), 256>>>(d_r, n, depth, extent, d_r2, d_kt);
+        PCK(cudaGetLastError());
     }
     const StampDev S{d_c, d_r2, d_kt, d_rgba};
     // level 0: the root and the stamps that touch the canvas

@@ -66,6 +66,12 @@ struct Ctx {
     unsigned long long host_hash = 0;
     std::vector<int64_t> level_begin;  // records of level l: [level_begin[l], level_begin[l + 1])
     bool uploaded = false;
+    // stamp table of a painted canvas (kept on the device for canvox_paint_append)
+    double* d_st_c = nullptr;
+    double* d_st_r = nullptr;
+    float4* d_st_rgba = nullptr;
+    int64_t st_n = 0, st_cap = 0;
+    bool painted = false;
     // views: device table and two pinned staging buffers, each guarded by an event
     View* d_views = nullptr;
     EyePath* d_eye = nullptr;
@@ -363,8 +369,53 @@ int drop_canvas() {
     g.d_leaves = nullptr;
     g.d_ropes = nullptr;
     g.uploaded = false;
+    g.painted = false;
     return CANVOX_OK;
 }
+
+// Room for n stamps in the device stamp table (keeps the first `keep` rows).
+int reserve_stamps(int64_t n, int64_t keep) {
+    if (n <= g.st_cap) return CANVOX_OK;
+    int64_t cap = 1024;
+    while (cap < n) cap *= 2;
+    double *c = nullptr, *r = nullptr;
+    float4* q = nullptr;
+    cudaError_t e = cudaMalloc(&c, sizeof(double) * 3 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&q, sizeof(float4) * (size_t)cap);
+    if (e == cudaSuccess && keep > 0) e = cudaMemcpy(c, g.d_st_c, sizeof(double) * 3 * (size_t)keep, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && keep > 0) e = cudaMemcpy(r, g.d_st_r, sizeof(double) * (size_t)keep, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && keep > 0) e = cudaMemcpy(q, g.d_st_rgba, sizeof(float4) * (size_t)keep, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(c);
+        cudaFree(r);
+        cudaFree(q);
+        return cuda_fail(e, "stamp table");
+    }
+    cudaFree(g.d_st_c);
+    cudaFree(g.d_st_r);
+    cudaFree(g.d_st_rgba);
+    g.d_st_c = c;
+    g.d_st_r = r;
+    g.d_st_rgba = q;
+    g.st_cap = cap;
+    return CANVOX_OK;
+}
+
+int check_stamps(const double* centers, const double* radii, const float* rgba, int64_t n) {
+    if (n < 0 || (n > 0 && (!centers || !radii || !rgba)) || n >= 0x7FFFFFFFll)
+        return fail(CANVOX_ERR_INVALID_ARG, "null stamp arrays or bad count");
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(centers[3 * i]) || !std::isfinite(centers[3 * i + 1]) || !std::isfinite(centers[3 * i + 2]) ||
+            !std::isfinite(radii[i]) || radii[i] < 0.0)
+            return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: non-finite centre or bad radius", (long long)i);
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(rgba[4 * i + c])) return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: non-finite colour", (long long)i);
+        if (rgba[4 * i + 3] < 0.0f) return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: negative extinction", (long long)i);
+    }
+    return CANVOX_OK;
+}
+
 
 // Neighbour links of the current pools, one launch per level (parents first).
 int build_links() {
@@ -372,6 +423,35 @@ int build_links() {
     for (size_t l = 0; l + 1 < g.level_begin.size(); ++l)
         CK(launch_rope_level(g.d_nodes, g.d_ropes, g.level_begin[l], g.level_begin[l + 1], (int)l, 0), "rope kernel launch");
     CK(cudaDeviceSynchronize(), "rope build");
+    return CANVOX_OK;
+}
+
+// Paint the device stamp table into new pools and make them the current canvas.
+int paint_table(int32_t depth, double extent, int64_t* n_records, int64_t* n_leaves) {
+    int32_t* nodes = nullptr;
+    uint2* leaves = nullptr;
+    int64_t nr = 0, nl = 0;
+    std::vector<int64_t> lb;
+    CK(paint_pools(depth, extent, g.d_st_c, g.d_st_r, g.d_st_rgba, g.st_n, &nodes, &leaves, &nr, &nl, &lb),
+       "device painter");
+    g.d_nodes = nodes;
+    g.d_leaves = leaves;
+    if (nr > 0x7FFFFFFFll || nl > 0x7FFFFFFFll) return fail(CANVOX_ERR_OOM, "painted canvas exceeds int32 pool indices");
+    g.n_rec = nr;
+    g.n_leaf = nl;
+    g.depth = depth;
+    g.extent = extent;
+    g.level_begin = lb;
+    // no host copy exists: the device hash stands for both
+    CK(cudaMemset(g.d_hash, 0, sizeof(unsigned long long)), "cudaMemset(hash)");
+    CK(launch_hash(device_tree(), g.d_hash, 0), "hash kernel launch");
+    CK(cudaMemcpy(&g.host_hash, g.d_hash, sizeof(unsigned long long), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
+    int rc = build_links();
+    if (rc) return rc;
+    g.uploaded = true;
+    g.painted = true;
+    if (n_records) *n_records = nr;
+    if (n_leaves) *n_leaves = nl;
     return CANVOX_OK;
 }
 
@@ -480,42 +560,40 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
 int canvox_paint_spheres(int32_t depth, double extent, const double* centers, const double* radii, const float* rgba,
                          int64_t n, int64_t* n_records, int64_t* n_leaves) {
     g_err.clear();
-    if (n < 0 || (n > 0 && (!centers || !radii || !rgba)) || n >= 0x7FFFFFFFll)
-        return fail(CANVOX_ERR_INVALID_ARG, "null stamp arrays or bad count");
-    int rc = check_canvas_args(depth, extent);
+    int rc = check_stamps(centers, radii, rgba, n);
     if (rc) return rc;
-    for (int64_t i = 0; i < n; ++i) {
-        if (!std::isfinite(centers[3 * i]) || !std::isfinite(centers[3 * i + 1]) || !std::isfinite(centers[3 * i + 2]) ||
-            !std::isfinite(radii[i]) || radii[i] < 0.0)
-            return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: non-finite centre or bad radius", (long long)i);
-        for (int c = 0; c < 4; ++c)
-            if (!std::isfinite(rgba[4 * i + c])) return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: non-finite colour", (long long)i);
-        if (rgba[4 * i + 3] < 0.0f) return fail(CANVOX_ERR_INVALID_ARG, "stamp %lld: negative extinction", (long long)i);
-    }
+    if ((rc = check_canvas_args(depth, extent))) return rc;
     if ((rc = ensure_device())) return rc;
     if ((rc = drop_canvas())) return rc;
-    int32_t* nodes = nullptr;
-    uint2* leaves = nullptr;
-    int64_t nr = 0, nl = 0;
-    std::vector<int64_t> lb;
-    CK(paint_pools(depth, extent, centers, radii, rgba, n, &nodes, &leaves, &nr, &nl, &lb), "device painter");
-    g.d_nodes = nodes;
-    g.d_leaves = leaves;
-    if (nr > 0x7FFFFFFFll || nl > 0x7FFFFFFFll) return fail(CANVOX_ERR_OOM, "painted canvas exceeds int32 pool indices");
-    g.n_rec = nr;
-    g.n_leaf = nl;
-    g.depth = depth;
-    g.extent = extent;
-    g.level_begin = lb;
-    // no host copy exists: the device hash stands for both
-    CK(cudaMemset(g.d_hash, 0, sizeof(unsigned long long)), "cudaMemset(hash)");
-    CK(launch_hash(device_tree(), g.d_hash, 0), "hash kernel launch");
-    CK(cudaMemcpy(&g.host_hash, g.d_hash, sizeof(unsigned long long), cudaMemcpyDeviceToHost), "cudaMemcpy(hash)");
-    if ((rc = build_links())) return rc;
-    g.uploaded = true;
-    if (n_records) *n_records = nr;
-    if (n_leaves) *n_leaves = nl;
-    return CANVOX_OK;
+    if ((rc = reserve_stamps(n, 0))) return rc;
+    if (n > 0) {
+        CK(cudaMemcpy(g.d_st_c, centers, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice), "cudaMemcpy(stamps)");
+        CK(cudaMemcpy(g.d_st_r, radii, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice), "cudaMemcpy(stamps)");
+        CK(cudaMemcpy(g.d_st_rgba, rgba, sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice), "cudaMemcpy(stamps)");
+    }
+    g.st_n = n;
+    return paint_table(depth, extent, n_records, n_leaves);
+}
+
+int canvox_paint_append(const double* centers, const double* radii, const float* rgba, int64_t n, int64_t* n_records,
+                        int64_t* n_leaves) {
+    g_err.clear();
+    if (!g.painted) return fail(CANVOX_ERR_NOT_UPLOADED, "the current canvas was not painted by canvox_paint_spheres");
+    int rc = check_stamps(centers, radii, rgba, n);
+    if (rc) return rc;
+    if (g.st_n + n >= 0x7FFFFFFFll) return fail(CANVOX_ERR_INVALID_ARG, "stamp table beyond 2^31 - 1 stamps");
+    const int32_t depth = g.depth;
+    const double extent = g.extent;
+    if ((rc = reserve_stamps(g.st_n + n, g.st_n))) return rc;
+    if (n > 0) {
+        CK(cudaMemcpy(g.d_st_c + 3 * g.st_n, centers, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice),
+           "cudaMemcpy(stamps)");
+        CK(cudaMemcpy(g.d_st_r + g.st_n, radii, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice), "cudaMemcpy(stamps)");
+        CK(cudaMemcpy(g.d_st_rgba + g.st_n, rgba, sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice), "cudaMemcpy(stamps)");
+    }
+    if ((rc = drop_canvas())) return rc;
+    g.st_n += n;
+    return paint_table(depth, extent, n_records, n_leaves);
 }
 
 int canvox_canvas_info(int64_t* n_records, int64_t* n_leaves, int32_t* depth, double* extent) {
@@ -846,6 +924,9 @@ void canvox_release(void) {
     if (g.d_scratch) cudaFree(g.d_scratch);
     if (g.d_hash) cudaFree(g.d_hash);
     if (g.d_host_out) cudaFree(g.d_host_out);
+    if (g.d_st_c) cudaFree(g.d_st_c);
+    if (g.d_st_r) cudaFree(g.d_st_r);
+    if (g.d_st_rgba) cudaFree(g.d_st_rgba);
     if (g.done) cudaEventDestroy(g.done);
     g = Ctx();
 }

@@ -73,3 +73,22 @@ def test_paint_rejects_bad_input():
     with pytest.raises(cx.CanvoxError):
         cx.paint_spheres(31, 1.0, [[0, 0, 0]], [0.1], [[1, 1, 1, 1]])
     _uploaded["key"] = None
+
+
+def test_paint_append_equals_whole_table():
+    """Painting stamps in two calls (the second appends) gives the pools of one call over the whole table,
+    the host painter's; an uploaded canvas cannot be appended to."""
+    D, E, c, r, q, _ = synth.config_stamps(0)
+    _uploaded["key"] = None
+    cx.paint_spheres(D, E, c[:600], r[:600], q[:600])
+    cx.paint_append(c[600:900], r[600:900], q[600:900])
+    nr, nl = cx.paint_append(c[900:], r[900:], q[900:])
+    ref = synth.build_config(0)
+    assert (nr, nl) == (ref.n_records, ref.n_leaves)
+    nodes, leaves = cx.download_octree()
+    np.testing.assert_array_equal(nodes, ref.nodes)
+    np.testing.assert_array_equal(leaves, ref.leaves)
+    cx.upload_octree(ref.nodes, ref.leaves, ref.depth, ref.extent)
+    with pytest.raises(cx.CanvoxError):
+        cx.paint_append(c[:1], r[:1], q[:1])
+    _uploaded["key"] = None
