@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default schedule")
     ap.add_argument("--res-scale", type=float, default=1.0, help="shrink every image side (profiling cases)")
     ap.add_argument("--n-fine", type=int, default=0, help="fine stamps of configs 2-4 (profiling cases; 0 = config)")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="with --impl reference: time the oracle once over the whole frame (all host cores)")
     return ap.parse_args()
 
 
@@ -203,6 +205,16 @@ def run_reference(args):
     cams = synth.config_cameras(cid)
     import oracle
     total = synth.total_pixels(cams)
+    if args.oracle_full:
+        t = time.perf_counter()
+        oracle.render(canvas, cams, threads=oracle.max_threads())
+        sec = time.perf_counter() - t
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": total / sec / 1e6, "unit": "Mrays/s",
+                          "config": {"workload": workload_name(cid), "rays_per_frame": total},
+                          "cpu_baseline": {"value": total / sec / 1e6, "unit": "Mrays/s", "cores": oracle.max_threads(),
+                                           "kind": "oracle", "sample": "the whole frame, once"},
+                          "seconds": sec}), flush=True)
+        return 0
     rng = np.random.default_rng(777)
     # each step: a bounded sample of the workload, sized so that warmup + steps end within minutes
     probe = rng.choice(total, size=512, replace=False).astype(np.int64)
