@@ -9,10 +9,11 @@
  * sizes and small structs; no C++ or PyTorch types cross this boundary.
  *
  * Threading and ownership: one global library context per process, bound to
- * the CUDA device that is current at canvox_upload_octree. Calls are not
- * thread-safe; serialise them. The library owns its device copy of the octree,
- * its camera staging buffers and its statistics buffer. The caller owns every
- * output buffer and every stream passed in.
+ * the CUDA device that is current at the first canvox_upload_octree or
+ * canvox_paint_spheres. Calls are not thread-safe; serialise them. The library
+ * owns its device copy of the octree (and, for a painted canvas, the stamp
+ * table), its camera staging buffers and its statistics buffer. The caller owns
+ * every output buffer and every stream passed in.
  *
  * Errors: every int-returning call returns CANVOX_OK (0) or a negative
  * CANVOX_ERR_* code and sets a message readable with canvox_last_error().
