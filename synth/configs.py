@@ -8,7 +8,8 @@ for config 0, metres for configs 1-4. Extinction sigma is per canvas unit.
       one 256x256 camera, 60 deg, outside the cube, looking at the centre; black background.
   c1  depth 16, 1 km cube, 100,000 spheres, r log-U[1 finest cell, 50 m];
       70 % sigma U[0.5,20]/m, 30 % sigma log-U[200,2000]/m (near-opaque);
-      one 1920x1080 camera, 60 deg, inside the cube, looking at the centre.
+      one 1920x1080 camera, 60 deg, inside the cube, looking at the centre, from the point of a 4 m grid
+      nearest (230, 110, -310) m that is 1 m clear of every sphere (the nominal point is inside paint).
   c2  depth 24, 40 km canvas (finest 2.4 mm): 10,000 background spheres r log-U[100 m, 1 km]
       (c1 extinction recipe, kept 10 m clear of the rooms) plus 200,000 fine spheres r log-U[2.4 mm, 10 cm]
       in four 1 m room boxes, extinction from an optical thickness 2 r sigma log-U[0.002, 0.2];
@@ -157,6 +158,19 @@ def _stereo_pair(head, yaw, pitch, scale, side, offset, bg):
     return cams
 
 
+def _clear_eye(eye, centers, radii, spacing=4.0, reach=60.0, clearance=1.0):
+    """The point of a grid (spacing, within reach of eye per axis) nearest eye that is at least clearance away
+    from every stamp sphere, so that the view does not start inside paint (ties: first in grid order)."""
+    g = np.arange(-reach, reach + spacing / 2, spacing)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    P = eye + np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    order = np.argsort(np.linalg.norm(P - eye, axis=1), kind="stable")
+    for p in P[order]:
+        if np.min(np.linalg.norm(centers - p, axis=1) - radii) > clearance:
+            return p
+    raise ValueError("no clear eye position near the nominal one")
+
+
 def config_cameras(cid, res_scale=1.0):
     """Camera records of a config. res_scale shrinks every image side (parity-test variants)."""
     def px(n):
@@ -167,7 +181,7 @@ def config_cameras(cid, res_scale=1.0):
         eye = 2.5 * d / np.linalg.norm(d)
         return cameras_array([look_at_camera(eye, [0, 0, 0], [0, 1, 0], math.tan(math.radians(30)), px(256), px(256))])
     if cid == 1:
-        eye = np.array([0.23, 0.11, -0.31]) * 1000.0
+        eye = _clear_eye(np.array([0.23, 0.11, -0.31]) * 1000.0, *config_stamps(1)[2:4])
         return cameras_array([look_at_camera(eye, [0, 0, 0], [0, 1, 0], math.tan(math.radians(30)),
                                              px(1920), px(1080), 0, SKY)])
     rng = Rng(SEED_BASE + 1000 + cid)
