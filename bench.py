@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default schedule")
     ap.add_argument("--res-scale", type=float, default=1.0, help="shrink every image side (profiling cases)")
     ap.add_argument("--n-fine", type=int, default=0, help="fine stamps of configs 2-4 (profiling cases; 0 = config)")
+    ap.add_argument("--paint-only", action="store_true",
+                    help="time the device stamp painter on the config's stamp table and exit")
     ap.add_argument("--oracle-full", action="store_true",
                     help="with --impl reference: time the oracle once over the whole frame (all host cores)")
     return ap.parse_args()
@@ -268,6 +270,17 @@ def main():
             dist.barrier()
 
     cid = args.config
+    if args.paint_only:
+        D_, E_, c_, r_, q_, _ = synth.config_stamps(cid, n_fine=args.n_fine or None)
+        cx.paint_spheres(D_, E_, c_[:8], r_[:8], q_[:8])   # warm-up (module load, allocator)
+        torch.cuda.synchronize()
+        t_dev = time.perf_counter()
+        nr_, nl_ = cx.paint_spheres(D_, E_, c_, r_, q_)
+        print(json.dumps({"metric": "device stamp painter", "value": time.perf_counter() - t_dev, "unit": "s",
+                          "higher_is_better": False, "config": {"workload": workload_name(cid),
+                                                                "stamps": int(r_.shape[0])},
+                          "records": nr_, "leaves": nl_}), flush=True)
+        return 0
     opts = json.loads(args.opts) if args.opts else {}
     t_host = time.perf_counter()
     canvas = synth.build_config(cid, n_fine=args.n_fine or None)
