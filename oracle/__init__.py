@@ -40,6 +40,9 @@ def lib():
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
         L.oracle_footprint.restype = ctypes.c_int64
+        L.oracle_walk32.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+        L.oracle_walk32.restype = ctypes.c_int64
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int32
         _lib = L
@@ -130,3 +133,23 @@ def footprint(canvas, cams, t_min=T_MIN_DEFAULT, threads=0):
     if rc != 0:
         raise RuntimeError(f"oracle_footprint returned {rc}")
     return rm[:nodes.shape[0]].astype(bool), lm[:canvas.n_leaves].astype(bool), out[:n]
+
+
+def walk32(canvas, cams, cell_local=True, threads=0, max_steps=0):
+    """The paper's FP32 walk (cell-local, or in canvas coordinates) to the canvas exit, geometry only.
+
+    Returns (steps int32 [n_pixels], angle_deg float64 [n_pixels]); pixels of no view: -1, NaN.
+    """
+    nodes = np.ascontiguousarray(canvas.nodes, dtype=np.int32)
+    cams = np.ascontiguousarray(cams)
+    n = 0
+    for c in cams:
+        n = max(n, int(c["out_offset_px"]) + int(c["width"]) * int(c["height"]))
+    steps = np.empty(max(n, 1), dtype=np.int32)
+    angle = np.empty(max(n, 1), dtype=np.float64)
+    rc = lib().oracle_walk32(nodes.ctypes.data, int(canvas.depth), float(canvas.extent),
+                             cams.ctypes.data if cams.shape[0] else None, int(cams.shape[0]), int(bool(cell_local)),
+                             int(max_steps), steps.ctypes.data, angle.ctypes.data, int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_walk32 returned {rc}")
+    return steps[:n], angle[:n]

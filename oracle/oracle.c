@@ -294,6 +294,199 @@ int64_t oracle_trace_rays(const int32_t *nodes, const uint16_t *leaves, int32_t 
     return bad;
 }
 
+/*
+ * The paper's single-precision walks (Sec. 6.2-6.3), geometry only, as the check of the
+ * GPU's implementation of them: the ray's position is carried in FP32, either in the
+ * frame of the current cell (cell_local = 1: origin at the cell centre, unit size,
+ * p in [-0.5, 0.5]) or in canvas coordinates (cell_local = 0). Each step leaves the
+ * cell at the nearest face, t = (face - p_a)/d_a, moves to p' = p + t d (the exit
+ * coordinate set to the face in the cell frame), finds the neighbour from integer
+ * cell coordinates, and re-expresses p' in the neighbour's frame: one cell over on
+ * the exit axis; for a finer neighbour, halving into the child the point lies in
+ * (2q -+ 1/2); for a coarser one, p' s + c with s the ratio of cell sizes and c the
+ * offset of the centres. Every FP32 operation is rounded on its own (no contraction).
+ * The start point is the canvas entry in FP64 (fma(t0, d, o)) rounded into the frame,
+ * and the start leaf is located in FP64 as in the ray caster above. The walk runs to
+ * the canvas exit (no compositing), and per output pixel writes the leaves visited
+ * and the angle in degrees between the pixel direction d and the line from the eye
+ * to the final position, atan2(|v x d|, v . d), v = X - o. Pixels of no view: -1, NaN.
+ */
+static float rel_face(float p, float d) { return (d > 0.0f ? 0.5f : -0.5f) - p; }
+
+int64_t oracle_walk32(const int32_t *nodes, int32_t depth, double extent, const ocam *cams, int32_t n_views,
+                      int32_t cell_local, int64_t max_steps, int32_t *steps_out, double *angle_out,
+                      int32_t n_threads) {
+    if (!nodes || depth < 1 || depth > 30 || !(extent > 0.0) || n_views < 0 || (n_views && !cams)) return -1;
+    if (max_steps <= 0) max_steps = 3 * ((int64_t)1 << depth) + 8;
+    const double E = extent, h = 0.5 * extent;
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        int64_t e = cams[v].out_offset_px + (int64_t)cams[v].width * cams[v].height;
+        if (e > total) total = e;
+    }
+    for (int64_t q = 0; q < total; ++q) {
+        steps_out[q] = -1;
+        angle_out[q] = NAN;
+    }
+    int64_t bad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#endif
+    for (int v = 0; v < n_views; ++v) {
+        const ocam *cm = &cams[v];
+        double f[3], u[3], r[3];
+        camera_frame(cm, f, u, r);
+        const int64_t npx = (int64_t)cm->width * cm->height;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
+#endif
+        for (int64_t local = 0; local < npx; ++local) {
+            double d64[3];
+            pixel_ray(cm, f, u, r, local % cm->width, local / cm->width, d64);
+            const double *o = cm->eye;
+            double t0 = 0.0, t1 = INFINITY;
+            int miss = 0;
+            for (int a = 0; a < 3; ++a) {
+                if (d64[a] != 0.0) {
+                    double ta = (-h - o[a]) / d64[a], tb = (h - o[a]) / d64[a];
+                    t0 = fmax(t0, d64[a] > 0.0 ? ta : tb);
+                    t1 = fmin(t1, d64[a] > 0.0 ? tb : ta);
+                } else if (!(o[a] >= -h && o[a] < h)) {
+                    miss = 1;
+                }
+            }
+            int32_t steps = 0;
+            double angle = 0.0;
+            if (!miss && t0 < t1) {
+                /* start leaf holding r(t0+) */
+                uint32_t c[3] = {0, 0, 0};
+                int L = 0;
+                int32_t rec = 0, slot;
+                for (;;) {
+                    double w = ldexp(E, -(L + 1));
+                    int k = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        double M = fma((double)(2u * c[a] + 1u), w, -h);
+                        uint32_t b = (uint32_t)high_side(M, o[a], d64[a], t0);
+                        c[a] = 2u * c[a] + b;
+                        k |= (int)b << a;
+                    }
+                    slot = nodes[8 * (int64_t)rec + k];
+                    ++L;
+                    if (slot <= 0) break;
+                    rec = slot;
+                }
+                const float d[3] = {(float)d64[0], (float)d64[1], (float)d64[2]};
+                float p[3];
+                double X[3];
+                for (int a = 0; a < 3; ++a) {
+                    double x = fma(t0, d64[a], o[a]);
+                    X[a] = x;
+                    if (cell_local) {
+                        double w = ldexp(E, -L);
+                        double centre = fma((double)c[a] + 0.5, w, -h);
+                        p[a] = (float)((x - centre) / w);
+                    } else {
+                        p[a] = (float)x;
+                    }
+                }
+                for (;;) {
+                    if (steps >= max_steps) { bad += 1; break; }
+                    steps += 1;
+                    const double w64 = ldexp(E, -L);
+                    float te = INFINITY;
+                    int ax = -1;
+                    for (int a = 0; a < 3; ++a) {
+                        if (d[a] == 0.0f) continue;
+                        float num = cell_local ? rel_face(p[a], d[a])
+                                               : (float)fma((double)(c[a] + (d[a] > 0.0f ? 1u : 0u)), w64, -h) - p[a];
+                        float ta = num / d[a];
+                        if (ta < te) { te = ta; ax = a; }
+                    }
+                    if (ax < 0) break;
+                    float pe[3];
+                    for (int a = 0; a < 3; ++a) {
+                        float m = te * d[a];
+                        pe[a] = p[a] + m;
+                    }
+                    if (cell_local) pe[ax] = d[ax] > 0.0f ? 0.5f : -0.5f;
+                    for (int a = 0; a < 3; ++a)
+                        X[a] = cell_local ? fma((double)c[a] + 0.5 + (double)pe[a], w64, -h) : (double)pe[a];
+                    const uint32_t up = d[ax] > 0.0f ? 1u : 0u;
+                    const uint32_t cn = up ? c[ax] + 1u : c[ax] - 1u;
+                    if ((cn >> L) != 0u) break;
+                    /* the neighbour: from the root by integer coordinates, at most level L */
+                    uint32_t cc[3] = {c[0], c[1], c[2]};
+                    cc[ax] = cn;
+                    int Ln = 0;
+                    rec = 0;
+                    for (int lev = 0;; ++lev) {
+                        int sh = L - 1 - lev, k = 0;
+                        for (int a = 0; a < 3; ++a) k |= (int)((cc[a] >> sh) & 1u) << a;
+                        slot = nodes[8 * (int64_t)rec + k];
+                        if (slot <= 0 || lev + 1 == L) { Ln = lev + 1; break; }
+                        rec = slot;
+                    }
+                    float qv[3] = {pe[0], pe[1], pe[2]};
+                    if (cell_local) qv[ax] = up ? -0.5f : 0.5f;
+                    int Lc = L;
+                    while (slot > 0) {
+                        /* finer neighbour: near side on the exit axis, the FP32 position on the others */
+                        rec = slot;
+                        int k = 0;
+                        double wc = ldexp(E, -(Lc + 1));
+                        for (int a = 0; a < 3; ++a) {
+                            uint32_t b;
+                            if (a == ax) {
+                                b = up ? 0u : 1u;
+                            } else if (cell_local) {
+                                b = qv[a] > 0.0f || (qv[a] == 0.0f && d[a] >= 0.0f);
+                            } else {
+                                float M = (float)fma((double)(2u * cc[a] + 1u), wc, -h);
+                                b = qv[a] > M || (qv[a] == M && d[a] >= 0.0f);
+                            }
+                            if (cell_local) {
+                                float twice = 2.0f * qv[a];
+                                qv[a] = twice - (b ? 0.5f : -0.5f);
+                            }
+                            cc[a] = 2u * cc[a] + b;
+                            k |= (int)b << a;
+                        }
+                        ++Lc;
+                        slot = nodes[8 * (int64_t)rec + k];
+                        Ln = Lc;
+                    }
+                    if (cell_local && Ln < L) {
+                        double s64 = ldexp(1.0, Ln - L);
+                        float sf = (float)s64;
+                        for (int a = 0; a < 3; ++a) {
+                            uint32_t cp = cc[a] >> (L - Ln);
+                            double off = ((double)cc[a] + 0.5) * s64 - ((double)cp + 0.5);
+                            float scaled = qv[a] * sf;
+                            qv[a] = scaled + (float)off;
+                        }
+                        qv[ax] = up ? -0.5f : 0.5f;
+                    }
+                    int shn = Lc - Ln;
+                    for (int a = 0; a < 3; ++a) {
+                        c[a] = cc[a] >> shn;
+                        p[a] = qv[a];
+                    }
+                    L = Ln;
+                }
+                double vv[3] = {X[0] - o[0], X[1] - o[1], X[2] - o[2]};
+                double cx = vv[1] * d64[2] - vv[2] * d64[1], cy = vv[2] * d64[0] - vv[0] * d64[2],
+                       cz = vv[0] * d64[1] - vv[1] * d64[0];
+                double dt = vv[0] * d64[0] + vv[1] * d64[1] + vv[2] * d64[2];
+                angle = atan2(sqrt(cx * cx + cy * cy + cz * cz), dt) * 57.29577951308232;
+            }
+            steps_out[cm->out_offset_px + local] = steps;
+            angle_out[cm->out_offset_px + local] = angle;
+        }
+    }
+    return bad;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int32_t oracle_max_threads(void) {
 #ifdef _OPENMP

@@ -265,3 +265,38 @@ def test_footprint_matches_bruteforce():
     assert rec_ref.sum() > 10 and leaf_ref.sum() > 10
     np.testing.assert_array_equal(rm, rec_ref)
     np.testing.assert_array_equal(lm, leaf_ref)
+
+
+def test_walk32_axis_aligned_rays_are_exact():
+    """The paper's FP32 walks on rays along an axis from dyadic points: every FP32 quantity is exact, so both
+    walks visit exactly the FP64 oracle's leaves and end on the axis (angle 0)."""
+    cv = rt.random_tree(6, seed=303, p_refine=0.55)
+    cams = []
+    off = 0
+    for eye, tgt in (([0.125, 0.3125, 1.5], [0.125, 0.3125, 0.0]), ([-2.0, 0.0625, -0.1875], [0.0, 0.0625, -0.1875]),
+                     ([0.4375, -1.75, 0.25], [0.4375, 0.0, 0.25])):
+        c = synth.look_at_camera(eye, tgt, [1, 0, 0] if eye[1] == -1.75 else [0, 1, 0], 0.3, 1, 1, off)
+        cams.append(c)
+        off += 1
+    cams = synth.cameras_array(cams)
+    _, ic, _ = oracle.render(cv, cams, t_min=0.0, counters=True)
+    for cell in (True, False):
+        st, an = oracle.walk32(cv, cams, cell_local=cell)
+        np.testing.assert_array_equal(st, ic[:, 0])
+        assert np.all(an == 0.0)
+
+
+def test_walk32_within_the_paper_bound():
+    """Cell-local FP32 walk (Sec. 6.2) on a general view: the ray-angle error stays within the paper's bound
+    asin(sqrt(2)(e0/L + 7.5 eps)) (Sec. 6.3), and the walk visits the FP64 oracle's leaves on almost every pixel."""
+    cv = synth.build_config(0)
+    cams = synth.config_cameras(0, res_scale=0.5)
+    _, ic, _ = oracle.render(cv, cams, t_min=0.0, counters=True)
+    st, an = oracle.walk32(cv, cams, cell_local=True)
+    hit = ic[:, 0] > 0
+    assert np.mean(st[hit] == ic[hit, 0]) > 0.99
+    eps = 2.0 ** -23
+    e0 = math.sqrt(3) * 2.0 ** -25 * 0.5
+    assert np.max(an) <= math.degrees(math.asin(math.sqrt(2) * (e0 / 1.5 + 7.5 * eps)))
+    st_w, an_w = oracle.walk32(cv, cams, cell_local=False)
+    assert np.max(an_w) > np.max(an)

@@ -72,3 +72,29 @@ def test_angle_error_cell_vs_canvas_coordinates(level):
     e0_16 = math.sqrt(3) * 2.0 ** -12 * s
     bound16 = math.degrees(math.asin(min(1.0, math.sqrt(2) * (e0_16 / s + 7.5 * EPS16))))
     assert np.all(np.isfinite(a16)) and np.max(a16) <= bound16
+
+
+@pytest.mark.parametrize("prec,cell_local", [(cx.PREC_CELL32, True), (cx.PREC_WORLD32, False)])
+def test_fp32_walks_match_the_oracle_walk(prec, cell_local):
+    """The GPU's FP32 walks against the oracle's (the same steps of Sec. 6.2 in FP32 on the CPU), run to the canvas
+    exit: the leaves visited per pixel agree exactly, the final angle to float rounding (and 1e-13 deg)."""
+    for key, cv, cams in (("c0", config_canvas(0), synth.config_cameras(0, res_scale=0.5)),
+                          (("deep", 23),) + _deep_views(23)):
+        n = synth.total_pixels(cams)
+        steps = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        ang = torch.full((n,), float("nan"), device="cuda")
+        render(cv, cams, key=key, precision=prec, t_min=0.0, step_count=steps, angle_deg=ang)
+        ref_steps, ref_ang = oracle.walk32(cv, cams, cell_local=cell_local)
+        np.testing.assert_array_equal(steps.cpu().numpy(), ref_steps)
+        # the final angle is evaluated in FP64 from a cross product that cancels for tiny angles; the compilers
+        # contract its products differently, which moves it by about 2^-52 rad (1e-14 deg) at most
+        np.testing.assert_allclose(ang.cpu().numpy().astype(np.float64), ref_ang.astype(np.float32).astype(np.float64),
+                                   rtol=2.0 ** -22, atol=1e-13)
+
+
+def _deep_views(level):
+    cv, lo, s = _embedded_scene(level)
+    centre = lo + 0.5 * s
+    cams = synth.cameras_array([
+        synth.look_at_camera(centre + np.array([1.3, 0.7, -1.9]) * s, centre, [0, 1, 0], 0.5, 48, 40, 0)])
+    return cv, cams
