@@ -92,3 +92,20 @@ def test_paint_append_equals_whole_table():
     with pytest.raises(cx.CanvoxError):
         cx.paint_append(c[:1], r[:1], q[:1])
     _uploaded["key"] = None
+
+
+def test_paint_ties_on_cell_planes():
+    """Stamps whose spheres touch cell faces, corners and centres exactly (distances equal to the radius) and whose
+    radius puts r/10 exactly on a cell size: every comparison of the painter meets its tie."""
+    D, E = 7, 1.0
+    w = E / 2.0 ** 4
+    c, r = [], []
+    for i in range(-3, 4):
+        for j in (-2, 0, 1):
+            c.append((i * w, j * w, 0.5 * w * (i % 2)))           # on planes and cell centres
+            r.append([w, 2 * w, 0.5 * w, 10 * w, 10 * E / 2.0 ** 6][(i + j) % 5])
+    c = np.array(c)
+    r = np.array(r)
+    rng = np.random.default_rng(11)
+    q = np.c_[rng.uniform(0, 1, (len(r), 3)), rng.uniform(0.5, 9.0, len(r))].astype(np.float32)
+    _paint_and_compare(D, E, c, r, q)
