@@ -6,10 +6,13 @@
 //
 // Cells are addressed by exact integer coordinates (level L, c in [0, 2^L)^3).
 // Crossing a face moves c by one on the exit axis; the lowest common ancestor
-// of the old and new cell is L - bitlength(c_old ^ c_new), and the new leaf is
-// found by re-descending from that ancestor's record, kept on a per-lane stack
-// of records by level. The integer bits fix the path down to the old cell's
-// level; only deeper levels need the ray's position.
+// of the old and new cell is L - bitlength(c_old ^ c_new). The new leaf is
+// found from the neighbouring cell: a sibling in the same record, else the
+// slot the parent's neighbour link names (the neighbour graph of Sec. 4.1.1,
+// built at upload), or, in the stack traversal, the ancestor's record kept on
+// a per-lane stack of records by level; then a descent while the cell is
+// internal. The integer bits fix the path down to the old cell's level; only
+// deeper levels need the ray's position.
 //
 // Precision (Sec. 6.1-6.3). The ray is evaluated inside a local frame, a cell
 // of level f <= L at most K levels above the leaf, in frame units:
