@@ -4,7 +4,8 @@
 // index pools, eight children per allocation unit, copied to the GPU), the
 // host/device bit-identity hash, per-view FP64 set-up of the eye and pixel
 // grid (Sec. 6.1), launch of the traversal kernels, CUDA-graph replay,
-// counters and the schedule autotuner.
+// counters, the schedule autotuner, the device painter's stamp table and the
+// measurement helpers' set-up.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

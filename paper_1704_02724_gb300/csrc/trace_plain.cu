@@ -1,13 +1,17 @@
-// Plain single-precision-type ray casters (one launch per view) and the pool hash.
+// Plain single-precision-type ray casters (one launch per view), and the small
+// kernels around the traversal: the pool hash, the eye leaf of each view, and
+// the neighbour links built at upload.
 //
 // These are the baselines the mixed kernel is measured against: the ray, the
 // cell planes and the compositing are all in one type R, in canvas
 // coordinates, and every step locates the leaf from the root (no stack, no
 // local frame). With R = double this is the plain FP64 GPU path; with
 // R = float it is the canvas-coordinate FP32 traversal that Sec. 6.3 and the
-// "canvas coordinate" panel of its accuracy figure show drifting at depth.
+// canvas-coordinate panel of its accuracy figure show drifting at depth.
 // Planes are formed from integer cell coordinates, c * w_L - E/2, so a plane has
 // one rounded value at every level and the located leaf always lies ahead of t.
+// The FP64 caster can also mark the records and stored leaves it reads (the
+// footprint of a frame, canvox_footprint).
 #include <cuda_fp16.h>
 
 #include "canvox_internal.cuh"
