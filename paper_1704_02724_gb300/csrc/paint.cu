@@ -134,6 +134,67 @@ __device__ __forceinline__ int classify_child(const ParentTerms& T, int k, doubl
     return d2 < r2 ? kPaint : kDrop;
 }
 
+// FP32 screen of the same box distances. Each coordinate difference to the low plane is formed in FP64 and
+// rounded once; the rest is FP32. Every FP32 distance is within `margin` of its FP64 counterpart (a generous
+// bound: differences within 2^-23 M_a, squares within 2^-21 M_a^2, two additions), so a comparison with r2
+// farther than `margin` decides as the FP64 one does; closer ones are retaken in FP64.
+struct FastTerms {
+    float dmin[2][3], dmax[2][3], cen[2][3];
+    float r2, margin;
+};
+
+__device__ __forceinline__ void fast_terms(const double* c, const double pl[3], float h, float hh, double r2,
+                                           FastTerms& F) {
+    float mm = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float dl = __double2float_rn(__dsub_rn(c[a], pl[a]));
+        const float dm = __fsub_rn(dl, h), du = __fsub_rn(dm, h);
+        const float A = __fmul_rn(dl, dl), B = __fmul_rn(dm, dm), C = __fmul_rn(du, du);
+        F.dmin[0][a] = dl < 0.0f ? A : (dm > 0.0f ? B : 0.0f);
+        F.dmin[1][a] = dm < 0.0f ? B : (du > 0.0f ? C : 0.0f);
+        F.dmax[0][a] = fmaxf(A, B);
+        F.dmax[1][a] = fmaxf(B, C);
+        const float el = __fsub_rn(dl, hh), em = __fsub_rn(dm, hh);
+        F.cen[0][a] = __fmul_rn(el, el);
+        F.cen[1][a] = __fmul_rn(em, em);
+        const float M = fabsf(dl) + 2.0f * h;
+        mm = __fmaf_rn(M, M, mm);
+    }
+    F.r2 = __double2float_rn(r2);
+    F.margin = 3.814697265625e-06f * mm + 2.384185791015625e-07f * F.r2;  // 2^-18 sum M^2 + 2^-22 r2
+}
+
+// kDrop / kPaint / kKeep when the screen decides, -1 when FP64 must.
+__device__ __forceinline__ int classify_fast(const FastTerms& F, int k, bool refined) {
+    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+    const float lo = F.r2 - F.margin, hi = F.r2 + F.margin;
+    const float dmin2 = (F.dmin[b0][0] + F.dmin[b1][1]) + F.dmin[b2][2];
+    if (dmin2 >= hi) return kDrop;
+    if (dmin2 >= lo) return -1;
+    const float dmax2 = (F.dmax[b0][0] + F.dmax[b1][1]) + F.dmax[b2][2];
+    if (dmax2 <= lo) return kPaint;
+    if (dmax2 <= hi) return -1;
+    if (refined) return kKeep;
+    const float d2 = (F.cen[b0][0] + F.cen[b1][1]) + F.cen[b2][2];
+    if (d2 < lo) return kPaint;
+    if (d2 >= hi) return kDrop;
+    return -1;
+}
+
+// Partial cover (the refining test): 1 / 0 when the screen decides, -1 when FP64 must.
+__device__ __forceinline__ int partial_fast(const FastTerms& F, int k) {
+    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+    const float lo = F.r2 - F.margin, hi = F.r2 + F.margin;
+    const float dmin2 = (F.dmin[b0][0] + F.dmin[b1][1]) + F.dmin[b2][2];
+    if (dmin2 >= hi) return 0;
+    if (dmin2 >= lo) return -1;
+    const float dmax2 = (F.dmax[b0][0] + F.dmax[b1][1]) + F.dmax[b2][2];
+    if (dmax2 <= lo) return 0;
+    if (dmax2 <= hi) return -1;
+    return 1;
+}
+
 __device__ __forceinline__ void parent_planes(const LevelIn& L, int64_t i, double extent, double half, double pl[3],
                                               double pm[3], double pu[3], double cl[3], double cm[3]) {
     const double H = extent * __longlong_as_double((long long)(1023 - L.level) << 52);
@@ -157,6 +218,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(Level
     if (i >= L.n) return;  // warp-uniform
     double pl[3], pm[3], pu[3], cl[3], cm[3];
     parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;  // child side and half side (exact)
     const int lc = L.level + 1;
     const int64_t b = L.off[i], e = L.off[i + 1];
     // the first refining stamp of each child
@@ -169,24 +231,31 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(Level
             const int64_t q = base + lane;
             int32_t v = -1;
             bool cand = false;
-            ParentTerms T;
+            FastTerms F;
             double r2 = 0.0;
             if (q < e) {
                 v = L.ent[q];
                 if (v >= 0 && S.kt[v] > lc) {
                     cand = true;
                     r2 = S.r2[v];
-                    parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                    fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
                 }
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 bool qual = false;
                 if (cand) {
-                    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
-                    const double dmin2 = __dadd_rn(__dadd_rn(T.dmin[b0][0], T.dmin[b1][1]), T.dmin[b2][2]);
-                    const double dmax2 = __dadd_rn(__dadd_rn(T.dmax[b0][0], T.dmax[b1][1]), T.dmax[b2][2]);
-                    qual = dmin2 < r2 && dmax2 > r2;
+                    const int f = partial_fast(F, k);
+                    if (f >= 0) {
+                        qual = f == 1;
+                    } else {
+                        ParentTerms T;
+                        parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                        const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+                        const double dmin2 = __dadd_rn(__dadd_rn(T.dmin[b0][0], T.dmin[b1][1]), T.dmin[b2][2]);
+                        const double dmax2 = __dadd_rn(__dadd_rn(T.dmax[b0][0], T.dmax[b1][1]), T.dmax[b2][2]);
+                        qual = dmin2 < r2 && dmax2 > r2;
+                    }
                 }
                 const unsigned m = __ballot_sync(kFullMask, qual);
                 const int32_t first = __shfl_sync(kFullMask, v, m ? __ffs(m) - 1 : 0);
@@ -206,14 +275,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(Level
         const int64_t q = base + lane;
         int32_t v = 0;
         bool valid = false;
-        ParentTerms T;
+        FastTerms F;
         double r2 = 0.0;
         if (q < e) {
             valid = true;
             v = L.ent[q];
             if (v >= 0) {
                 r2 = S.r2[v];
-                parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
             }
         }
         s_idx[wib][lane] = v < 0 ? ~v : v;
@@ -222,7 +291,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(Level
         for (int k = 0; k < 8; ++k) {
             const bool internal = fr[k] != 0x7FFFFFFF;
             int c = kDrop;
-            if (valid) c = v < 0 ? kPaint : classify_child(T, k, r2, internal && fr[k] <= v);
+            if (valid) {
+                if (v < 0) {
+                    c = kPaint;
+                } else {
+                    const bool refined = internal && fr[k] <= v;
+                    c = classify_fast(F, k, refined);
+                    if (c < 0) {
+                        ParentTerms T;
+                        parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                        c = classify_child(T, k, r2, refined);
+                    }
+                }
+            }
             if (internal) {
                 n[k] += __popc(__ballot_sync(kFullMask, c != kDrop));
             } else {
@@ -292,26 +373,38 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_write(Level
     }
     double pl[3], pm[3], pu[3], cl[3], cm[3];
     parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
     const int64_t b = L.off[i], e = L.off[i + 1];
     for (int64_t base = b; base < e; base += 32) {
         const int64_t q = base + lane;
         int32_t v = 0;
         bool valid = false;
-        ParentTerms T;
+        FastTerms F;
         double r2 = 0.0;
         if (q < e) {
             valid = true;
             v = L.ent[q];
             if (v >= 0) {
                 r2 = S.r2[v];
-                parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
             }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if (!((internal >> k) & 1u)) continue;  // warp-uniform
             int c = kDrop;
-            if (valid) c = v < 0 ? kPaint : classify_child(T, k, r2, fr[k] <= v);
+            if (valid) {
+                if (v < 0) {
+                    c = kPaint;
+                } else {
+                    c = classify_fast(F, k, fr[k] <= v);
+                    if (c < 0) {
+                        ParentTerms T;
+                        parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                        c = classify_child(T, k, r2, fr[k] <= v);
+                    }
+                }
+            }
             const bool keep = c != kDrop;
             const unsigned m = __ballot_sync(kFullMask, keep);
             if (keep) nent[w[k] + __popc(m & ((1u << lane) - 1u))] = (v < 0 || c == kKeep) ? v : ~v;
