@@ -98,6 +98,7 @@ enum { kDrop = 0, kPaint = 1, kKeep = 2 };
 // Lanes take a cell's stamp list 32 entries at a time, in order.
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kWarpsPerBlock = 4;
+constexpr int64_t kSplitCells = 8192;  // levels with fewer refined cells take one warp per child
 
 // One warp per refined cell, all eight children at once. Per axis a stamp's squared distances to the
 // cell's three planes (low, mid, high) serve both halves, so a child's box distances are sums of
@@ -122,15 +123,20 @@ __device__ __forceinline__ void parent_terms(const double* c, const double pl[3]
     }
 }
 
+// Term of child k on axis a (the half it lies in), picked without indexing by a runtime value.
+template <typename V>
+__device__ __forceinline__ V half_term(const V (&x)[2][3], int k, int a) {
+    return ((k >> a) & 1) ? x[1][a] : x[0][a];
+}
+
 // Child k: kDrop / kPaint / kKeep for an undecided stamp with squared radius r2.
 __device__ __forceinline__ int classify_child(const ParentTerms& T, int k, double r2, bool refined) {
-    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
-    const double dmin2 = __dadd_rn(__dadd_rn(T.dmin[b0][0], T.dmin[b1][1]), T.dmin[b2][2]);
+    const double dmin2 = __dadd_rn(__dadd_rn(half_term(T.dmin, k, 0), half_term(T.dmin, k, 1)), half_term(T.dmin, k, 2));
     if (dmin2 >= r2) return kDrop;
-    const double dmax2 = __dadd_rn(__dadd_rn(T.dmax[b0][0], T.dmax[b1][1]), T.dmax[b2][2]);
+    const double dmax2 = __dadd_rn(__dadd_rn(half_term(T.dmax, k, 0), half_term(T.dmax, k, 1)), half_term(T.dmax, k, 2));
     if (dmax2 <= r2) return kPaint;
     if (refined) return kKeep;
-    const double d2 = __dadd_rn(__dadd_rn(T.cen[b0][0], T.cen[b1][1]), T.cen[b2][2]);
+    const double d2 = __dadd_rn(__dadd_rn(half_term(T.cen, k, 0), half_term(T.cen, k, 1)), half_term(T.cen, k, 2));
     return d2 < r2 ? kPaint : kDrop;
 }
 
@@ -167,16 +173,15 @@ __device__ __forceinline__ void fast_terms(const double* c, const double pl[3], 
 
 // kDrop / kPaint / kKeep when the screen decides, -1 when FP64 must.
 __device__ __forceinline__ int classify_fast(const FastTerms& F, int k, bool refined) {
-    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
     const float lo = F.r2 - F.margin, hi = F.r2 + F.margin;
-    const float dmin2 = (F.dmin[b0][0] + F.dmin[b1][1]) + F.dmin[b2][2];
+    const float dmin2 = (half_term(F.dmin, k, 0) + half_term(F.dmin, k, 1)) + half_term(F.dmin, k, 2);
     if (dmin2 >= hi) return kDrop;
     if (dmin2 >= lo) return -1;
-    const float dmax2 = (F.dmax[b0][0] + F.dmax[b1][1]) + F.dmax[b2][2];
+    const float dmax2 = (half_term(F.dmax, k, 0) + half_term(F.dmax, k, 1)) + half_term(F.dmax, k, 2);
     if (dmax2 <= lo) return kPaint;
     if (dmax2 <= hi) return -1;
     if (refined) return kKeep;
-    const float d2 = (F.cen[b0][0] + F.cen[b1][1]) + F.cen[b2][2];
+    const float d2 = (half_term(F.cen, k, 0) + half_term(F.cen, k, 1)) + half_term(F.cen, k, 2);
     if (d2 < lo) return kPaint;
     if (d2 >= hi) return kDrop;
     return -1;
@@ -184,12 +189,11 @@ __device__ __forceinline__ int classify_fast(const FastTerms& F, int k, bool ref
 
 // Partial cover (the refining test): 1 / 0 when the screen decides, -1 when FP64 must.
 __device__ __forceinline__ int partial_fast(const FastTerms& F, int k) {
-    const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
     const float lo = F.r2 - F.margin, hi = F.r2 + F.margin;
-    const float dmin2 = (F.dmin[b0][0] + F.dmin[b1][1]) + F.dmin[b2][2];
+    const float dmin2 = (half_term(F.dmin, k, 0) + half_term(F.dmin, k, 1)) + half_term(F.dmin, k, 2);
     if (dmin2 >= hi) return 0;
     if (dmin2 >= lo) return -1;
-    const float dmax2 = (F.dmax[b0][0] + F.dmax[b1][1]) + F.dmax[b2][2];
+    const float dmax2 = (half_term(F.dmax, k, 0) + half_term(F.dmax, k, 1)) + half_term(F.dmax, k, 2);
     if (dmax2 <= lo) return 0;
     if (dmax2 <= hi) return -1;
     return 1;
@@ -251,9 +255,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(Level
                     } else {
                         ParentTerms T;
                         parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
-                        const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
-                        const double dmin2 = __dadd_rn(__dadd_rn(T.dmin[b0][0], T.dmin[b1][1]), T.dmin[b2][2]);
-                        const double dmax2 = __dadd_rn(__dadd_rn(T.dmax[b0][0], T.dmax[b1][1]), T.dmax[b2][2]);
+                        const double dmin2 = __dadd_rn(__dadd_rn(half_term(T.dmin, k, 0), half_term(T.dmin, k, 1)),
+                                                       half_term(T.dmin, k, 2));
+                        const double dmax2 = __dadd_rn(__dadd_rn(half_term(T.dmax, k, 0), half_term(T.dmax, k, 1)),
+                                                       half_term(T.dmax, k, 2));
                         qual = dmin2 < r2 && dmax2 > r2;
                     }
                 }
@@ -427,6 +432,163 @@ __global__ void stamp_prep(const double* r, int64_t n, int32_t depth, double ext
         ++k;
     }
     kt[s] = k;
+}
+
+// The same two passes with one warp per child, for levels of few refined cells: near the root and around the
+// rooms a cell's list holds tens of thousands of stamps, and eight warps per cell instead of one keep the GPU
+// busy. The per-child decisions are the ones above (the same screen and FP64 fallback), so the output is too.
+__device__ __forceinline__ int child_class(const StampDev& S, const FastTerms& F, int32_t v, double r2, int k,
+                                           bool refined, const double pl[3], const double pm[3], const double pu[3],
+                                           const double cl[3], const double cm[3]) {
+    int c = classify_fast(F, k, refined);
+    if (c < 0) {
+        ParentTerms T;
+        parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+        c = classify_child(T, k, r2, refined);
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_child_count(LevelIn L, StampDev S, int32_t depth,
+                                                                          double extent, double half, int32_t* firstref,
+                                                                          uint64_t* slot, int64_t* count, int64_t* is_int) {
+    __shared__ int32_t s_idx[kWarpsPerBlock][32];
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (t >= 8 * L.n) return;  // warp-uniform
+    const int64_t i = t >> 3;
+    const int k = (int)(t & 7);
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
+    const int lc = L.level + 1;
+    const int64_t b = L.off[i], e = L.off[i + 1];
+    int32_t fr = 0x7FFFFFFF;
+    if (lc < depth) {
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t q = base + lane;
+            int32_t v = -1;
+            bool qual = false;
+            if (q < e) {
+                v = L.ent[q];
+                if (v >= 0 && S.kt[v] > lc) {
+                    const double r2 = S.r2[v];
+                    FastTerms F;
+                    fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
+                    const int f = partial_fast(F, k);
+                    if (f >= 0) {
+                        qual = f == 1;
+                    } else {
+                        ParentTerms T;
+                        parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+                        const double dmin2 = __dadd_rn(__dadd_rn(half_term(T.dmin, k, 0), half_term(T.dmin, k, 1)),
+                                                       half_term(T.dmin, k, 2));
+                        const double dmax2 = __dadd_rn(__dadd_rn(half_term(T.dmax, k, 0), half_term(T.dmax, k, 1)),
+                                                       half_term(T.dmax, k, 2));
+                        qual = dmin2 < r2 && dmax2 > r2;
+                    }
+                }
+            }
+            const unsigned m = __ballot_sync(kFullMask, qual);
+            if (m) {
+                fr = __shfl_sync(kFullMask, v, __ffs(m) - 1);  // entries are in stamp order
+                break;
+            }
+        }
+    }
+    int64_t n = 0;
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t q = base + lane;
+        int32_t v = 0;
+        int c = kDrop;
+        if (q < e) {
+            v = L.ent[q];
+            if (v < 0) {
+                c = kPaint;
+            } else {
+                const double r2 = S.r2[v];
+                FastTerms F;
+                fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
+                c = child_class(S, F, v, r2, k, fr != 0x7FFFFFFF && fr <= v, pl, pm, pu, cl, cm);
+            }
+        }
+        if (fr != 0x7FFFFFFF) {
+            n += __popc(__ballot_sync(kFullMask, c != kDrop));
+        } else {
+            s_idx[wib][lane] = v < 0 ? ~v : v;
+            unsigned m = __ballot_sync(kFullMask, c == kPaint);
+            __syncwarp();
+            while (m) {  // every lane folds the same sequence
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                blend(val, S.rgba[s_idx[wib][j]]);
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        firstref[t] = fr;
+        if (fr != 0x7FFFFFFF) {
+            count[t] = n;
+            is_int[t] = 1;
+            slot[t] = kInternal;
+        } else {
+            count[t] = 0;
+            is_int[t] = 0;
+            slot[t] = leaf_key(val);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_child_write(LevelIn L, StampDev S, double extent,
+                                                                          double half, const int32_t* firstref,
+                                                                          uint64_t* slot, const int64_t* ent_off,
+                                                                          const int64_t* next_idx, uint32_t* ncoord,
+                                                                          int64_t* noff, int32_t* nent) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= 8 * L.n) return;
+    if (slot[t] != kInternal) return;  // warp-uniform
+    const int64_t i = t >> 3;
+    const int k = (int)(t & 7);
+    const int32_t fr = firstref[t];
+    const int64_t j = next_idx[t];
+    int64_t w = ent_off[t];
+    __syncwarp();
+    if (lane == 0) {
+        slot[t] = kInternal | (uint64_t)j;
+        ncoord[3 * j] = 2u * L.coord[3 * i] + (k & 1u);
+        ncoord[3 * j + 1] = 2u * L.coord[3 * i + 1] + ((k >> 1) & 1u);
+        ncoord[3 * j + 2] = 2u * L.coord[3 * i + 2] + ((k >> 2) & 1u);
+        noff[j] = w;
+    }
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
+    const int64_t b = L.off[i], e = L.off[i + 1];
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t q = base + lane;
+        int32_t out = 0;
+        bool keep = false;
+        if (q < e) {
+            const int32_t v = L.ent[q];
+            if (v < 0) {
+                out = v;
+                keep = true;
+            } else {
+                const double r2 = S.r2[v];
+                FastTerms F;
+                fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
+                const int c = child_class(S, F, v, r2, k, fr <= v, pl, pm, pu, cl, cm);
+                keep = c != kDrop;
+                out = c == kPaint ? ~v : v;
+            }
+        }
+        const unsigned m = __ballot_sync(kFullMask, keep);
+        if (keep) nent[w + __popc(m & ((1u << lane) - 1u))] = out;
+        w += __popc(m);
+    }
 }
 
 // Stamps that touch the canvas, in order (the root's list).
@@ -647,8 +809,13 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const d
         PCK(buf.alloc(&slot, nch));
         PCK(buf.alloc(&cnt, nch));
         PCK(buf.alloc(&isint, nch));
-        expand_parent_count<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr, slot,
-                                                                                       cnt, isint);
+        const bool split = L.n < kSplitCells;  // few cells: a warp per child
+        if (split)
+            expand_child_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr,
+                                                                                        slot, cnt, isint);
+        else
+            expand_parent_count<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr,
+                                                                                         slot, cnt, isint);
         PCK(cudaGetLastError());
         int64_t n_ent = 0, n_next = 0;
         PCK(scan_i64(cnt, nch, &n_ent));
@@ -668,8 +835,12 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const d
         PCK(buf.alloc(&noff, n_next + 1));
         PCK(buf.alloc(&nent, n_ent));
         PCK(cudaMemcpy(noff + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
-        expand_parent_write<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot, cnt,
-                                                                                       isint, ncoord, noff, nent);
+        if (split)
+            expand_child_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot, cnt,
+                                                                                        isint, ncoord, noff, nent);
+        else
+            expand_parent_write<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot,
+                                                                                         cnt, isint, ncoord, noff, nent);
         PCK(cudaGetLastError());
         PCK(cudaDeviceSynchronize());
         buf.release(fr);
