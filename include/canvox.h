@@ -204,6 +204,21 @@ int canvox_canvas_info(int64_t* n_records, int64_t* n_leaves, int32_t* depth, do
 int canvox_download_octree(int32_t* node_pool, uint16_t* leaf_rgba);
 
 /*
+ * Replace the values of leaves [first, first + count) of the current canvas with
+ * leaf_rgba (host uint16[count][4], the layout of canvox_upload_octree); the tree
+ * structure is unchanged. This is the dirty-range upload of a value edit (recolouring
+ * or re-weighting paint without refining or merging cells, Sec. 4.1's editing of the
+ * colour pool): only the changed range crosses the bus. The values are validated as at
+ * upload (finite, extinction >= 0; CANVOX_ERR_BAD_TREE, nothing changed); the range
+ * must lie in the pool (CANVOX_ERR_INVALID_ARG). Synchronous: waits for earlier
+ * renders; the host-side pool hash is updated, so canvox_octree_hash still compares
+ * the device copy with the values the caller supplied. A structural edit (cells
+ * refined or merged) renumbers the breadth-first pools from the first change on:
+ * upload again, or repaint with canvox_paint_append.
+ */
+int canvox_update_leaves(int64_t first, int64_t count, const uint16_t* leaf_rgba);
+
+/*
  * Render n_views views into out_rgba_dev (device float32 RGBA, at least
  * max(out_offset_px + width * height) pixels, 16 bytes each), stream-ordered
  * on `stream` (a cudaStream_t; NULL = legacy default stream) with the default

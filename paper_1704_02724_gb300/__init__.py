@@ -26,6 +26,7 @@ from .canvox import (  # noqa: F401
     paint_spheres,
     paint_append,
     canvas_info,
+    update_leaves,
     download_octree,
     probe_l2_gather,
     probe_fp64,

@@ -106,6 +106,8 @@ def lib():
         L.canvox_paint_spheres.restype = ctypes.c_int
         L.canvox_paint_append.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.canvox_paint_append.restype = ctypes.c_int
+        L.canvox_update_leaves.argtypes = [i64, i64, vp]
+        L.canvox_update_leaves.restype = ctypes.c_int
         L.canvox_canvas_info.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.canvox_canvas_info.restype = ctypes.c_int
@@ -263,6 +265,12 @@ def paint_append(centers, radii, rgba):
     _check(lib().canvox_paint_append(c.ctypes.data if n else None, r.ctypes.data if n else None,
                                      q.ctypes.data if n else None, n, ctypes.byref(nr), ctypes.byref(nl)))
     return nr.value, nl.value
+
+
+def update_leaves(first, leaf_rgba):
+    """canvox_update_leaves: new values for leaves [first, first + len(leaf_rgba)) of the current canvas."""
+    q = np.ascontiguousarray(leaf_rgba, dtype=np.uint16).reshape(-1, 4)
+    _check(lib().canvox_update_leaves(int(first), q.shape[0], q.ctypes.data if q.size else None))
 
 
 def canvas_info():

@@ -618,6 +618,39 @@ int canvox_download_octree(int32_t* node_pool, uint16_t* leaf_rgba) {
     return CANVOX_OK;
 }
 
+int canvox_update_leaves(int64_t first, int64_t count, const uint16_t* leaf_rgba) {
+    g_err.clear();
+    if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");
+    if (count < 0 || first < 0 || first > g.n_leaf || count > g.n_leaf - first || (count > 0 && !leaf_rgba))
+        return fail(CANVOX_ERR_INVALID_ARG, "leaf range [%lld, %lld) outside the pool of %lld leaves",
+                    (long long)first, (long long)(first + count), (long long)g.n_leaf);
+    for (int64_t i = 0; i < count; ++i) {
+        const uint16_t* q = leaf_rgba + 4 * i;
+        for (int c = 0; c < 4; ++c)
+            if (((q[c] >> 10) & 31) == 31) return fail(CANVOX_ERR_BAD_TREE, "leaf %lld: non-finite FP16", (long long)(first + i));
+        if ((q[3] & 0x8000u) && (q[3] & 0x7FFFu))
+            return fail(CANVOX_ERR_BAD_TREE, "leaf %lld: negative extinction", (long long)(first + i));
+    }
+    if (count == 0) return CANVOX_OK;
+    if (g.any_render) CK(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    // the pool hash is a sum over elements: take the old values' terms out, put the new ones in
+    std::vector<uint2> old((size_t)count);
+    CK(cudaMemcpy(old.data(), g.d_leaves + first, sizeof(uint2) * (size_t)count, cudaMemcpyDeviceToHost), "cudaMemcpy(leaves)");
+    unsigned long long hh = g.host_hash;
+    for (int64_t i = 0; i < count; ++i) {
+        const uint16_t* q = leaf_rgba + 4 * i;
+        const unsigned long long nv = (unsigned long long)q[0] | ((unsigned long long)q[1] << 16) |
+                                      ((unsigned long long)q[2] << 32) | ((unsigned long long)q[3] << 48);
+        const unsigned long long ov = ((unsigned long long)old[(size_t)i].y << 32) | old[(size_t)i].x;
+        hh -= elem_hash(2ull, (unsigned long long)(first + i), ov);
+        hh += elem_hash(2ull, (unsigned long long)(first + i), nv);
+    }
+    CK(cudaMemcpy(g.d_leaves + first, leaf_rgba, sizeof(uint2) * (size_t)count, cudaMemcpyHostToDevice), "cudaMemcpy(leaves)");
+    g.host_hash = hh;
+    g.last_h2d = (int64_t)sizeof(uint2) * count;
+    return CANVOX_OK;
+}
+
 int canvox_octree_hash(uint64_t* host_hash, uint64_t* device_hash) {
     g_err.clear();
     if (!g.uploaded) return fail(CANVOX_ERR_NOT_UPLOADED, "no canvas uploaded");

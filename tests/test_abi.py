@@ -68,6 +68,12 @@ def test_host_paths_without_gpu(L):
     with pytest.raises(cx.CanvoxError) as e:
         cx.octree_hash()
     assert e.value.code == canvox.ERR_NOT_UPLOADED
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.update_leaves(0, np.zeros((1, 4), np.uint16))
+    assert e.value.code == canvox.ERR_NOT_UPLOADED
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.paint_append(np.zeros((1, 3)), [0.1], [[1, 1, 1, 1]])
+    assert e.value.code == canvox.ERR_NOT_UPLOADED
 
 
 def _expect(code, nodes, leaves, depth=4, extent=1.0):

@@ -269,6 +269,38 @@ def test_empty_canvas_zero_views_and_bad_cameras():
     assert e.value.code == canvox.ERR_INVALID_ARG
 
 
+def test_update_leaves_equals_full_upload():
+    """A value edit uploaded as a dirty leaf range renders (bit for bit) and hashes like the edited pools
+    uploaded whole; a bad range or value changes nothing."""
+    cv = config_canvas(0)
+    cams = synth.config_cameras(0, res_scale=0.5)
+    edited = cv.leaves.copy()
+    lo, hi = 100_000, 140_000
+    vals = edited[lo:hi].view(np.float16).astype(np.float32)
+    vals[:, 0:3] = vals[:, [2, 0, 1]]          # recolour
+    vals[:, 3] *= 0.25                          # thinner paint
+    edited[lo:hi] = vals.astype(np.float16).view(np.uint16)
+    upload(cv, "c0")
+    cx.update_leaves(lo, edited[lo:hi])
+    h, d = cx.octree_hash()
+    assert h == d
+    img, _ = render(cv, cams, key="c0")         # the cached upload, edited in place
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.update_leaves(cv.n_leaves - 1, edited[:2])
+    assert e.value.code == canvox.ERR_INVALID_ARG
+    bad = edited[lo:lo + 1].copy()
+    bad[0, 3] = np.float16(-1.0).view(np.uint16)
+    with pytest.raises(cx.CanvoxError) as e:
+        cx.update_leaves(lo, bad)
+    assert e.value.code == canvox.ERR_BAD_TREE
+    assert cx.octree_hash() == (h, d)
+    whole = synth.Canvas(nodes=cv.nodes, leaves=edited, depth=cv.depth, extent=cv.extent, levels=cv.levels, info={})
+    ref, _ = render(whole, cams, key="c0_edited_whole")
+    np.testing.assert_array_equal(img, ref)
+    assert cx.octree_hash() == (h, d)
+    assert max_err(img, oracle.render(whole, cams)) <= TOL
+
+
 def test_bad_upload_keeps_previous_canvas():
     cv = config_canvas(0)
     upload(cv, "c0")
