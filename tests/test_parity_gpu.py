@@ -173,16 +173,25 @@ def _sample_pixels(cams, n_random, n_tiles, seed):
 
 @pytest.mark.parametrize("cid,n_random", [(1, 100000), (2, 300000), (3, 200000), (4, 200000)])
 def test_full_size_sampled(cid, n_random):
-    """Full-size images in the benchmark's launch configuration; oracle on sampled pixels."""
+    """Full-size images with the built-in schedule and with the one the autotuner picks for these views (the
+    schedule bench.py times); oracle on sampled pixels."""
+    from gpu_util import _uploaded
     cv = config_canvas(cid)
     cams = synth.config_cameras(cid)
-    img, st = render(cv, cams, key=f"c{3 if cid == 4 else cid}")
-    assert st["status"] == 0
+    key = f"c{3 if cid == 4 else cid}"
     px = _sample_pixels(cams, n_random, 2, seed=cid)
     ref = oracle.render(cv, cams, px_idx=px)
-    err = np.abs(img[px] - ref)
-    assert float(err.max()) <= TOL, (float(err.max()), int(np.sum(err.max(1) > TOL)))
-    assert np.all(np.isfinite(img))
+    img, st = render(cv, cams, key=key)
+    upload(cv, key)
+    best = cx.autotune(cams)
+    img_tuned, st_tuned = render(cv, cams, key=key, **{k: best[k] for k in ("tile_w", "frame_levels", "traversal")})
+    cx.release()                     # back to the built-in schedule for the tests that follow
+    _uploaded["key"] = None
+    for im, s_ in ((img, st), (img_tuned, st_tuned)):
+        assert s_["status"] == 0
+        err = np.abs(im[px] - ref)
+        assert float(err.max()) <= TOL, (float(err.max()), int(np.sum(err.max(1) > TOL)), best)
+        assert np.all(np.isfinite(im))
 
 
 def test_schedules_agree_bitwise():
