@@ -130,6 +130,24 @@ def test_deep_embedding_mixed_passes_fp32_fails(level):
         assert max_err(img32, ref) > 1e-3   # canvas-coordinate FP32 drifts at this depth
 
 
+@pytest.mark.parametrize("frames,traversal", [(2, 0), (3, 1), (8, 0), (8, 1)])
+def test_small_frames_rebase_often(frames, traversal):
+    """Frames only a few levels deep make nearly every descent and many crossings rebase the ray (FP64 frame
+    set-ups): the images stay within the bar on c0 and on the scene embedded at depth 23, with both traversals."""
+    cv, lo, s = _embedded_scene(23)
+    centre = lo + 0.5 * s
+    deep_cams = synth.cameras_array([
+        synth.look_at_camera(centre + np.array([1.3, 0.7, -1.9]) * s, centre, [0, 1, 0], 0.5, 48, 40, 0),
+        synth.look_at_camera(centre + np.array([0.1, -0.2, 0.15]) * s, centre + np.array([0.4, 0.3, -0.2]) * s,
+                             [0, 1, 0], 1.0, 32, 32, 48 * 40)])
+    for key, canvas, cams in ((("deep", 23), cv, deep_cams), ("c0", config_canvas(0), synth.config_cameras(0, 0.5))):
+        ref = oracle.render(canvas, cams)
+        img, st = render(canvas, cams, key=key, frame_levels=frames, traversal=traversal)
+        if key != "c0" or frames < 8:    # (c0 is 8 levels deep: 8-level frames never need a rebase there)
+            assert st["rebases"] > st["rays"]
+        assert max_err(img, ref) <= TOL, (key, frames, traversal)
+
+
 def test_root_array_canvas():
     """A canvas whose top two levels are refined everywhere (the 4^3 array of octree roots of Sec. 4):
     the mixed path against the oracle, and the same image as the merged canvas of the same strokes."""
