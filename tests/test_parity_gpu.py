@@ -148,6 +148,34 @@ def test_small_frames_rebase_often(frames, traversal):
         assert max_err(img, ref) <= TOL, (key, frames, traversal)
 
 
+@pytest.mark.parametrize("budget", [0.0, 1.0])
+def test_error_budget_extremes(budget):
+    """err_budget 0 takes every boundary between different leaves in FP64 (the fallback path on every step),
+    err_budget 1 never does; both stay within the bar."""
+    cv, lo, s = _embedded_scene(26)
+    centre = lo + 0.5 * s
+    cams = synth.cameras_array([
+        synth.look_at_camera(centre + np.array([1.3, 0.7, -1.9]) * s, centre, [0, 1, 0], 0.5, 48, 40, 0)])
+    ref = oracle.render(cv, cams)
+    img, st = render(cv, cams, key=("deep", 26), err_budget=budget)
+    if budget == 0.0:
+        assert st["fp64_boundaries"] > st["rays"]
+    assert max_err(img, ref) <= TOL
+
+
+def test_graph_cache_follows_the_view_layout():
+    """Graph replay with one view layout, then another, then the first again: every render matches the
+    direct launch of the same views (the cached graph is keyed on sizes, offsets, output and options)."""
+    cv = config_canvas(0)
+    a = _edge_cameras(1.0)
+    b = synth.config_cameras(0, res_scale=0.5)
+    ref_a, _ = render(cv, a, key="c0")
+    ref_b, _ = render(cv, b, key="c0")
+    for cams, ref in ((a, ref_a), (b, ref_b), (a, ref_a), (b, ref_b)):
+        img, _ = render(cv, cams, key="c0", use_graph=1)
+        np.testing.assert_array_equal(img, ref)
+
+
 def test_root_array_canvas():
     """A canvas whose top two levels are refined everywhere (the 4^3 array of octree roots of Sec. 4):
     the mixed path against the oracle, and the same image as the merged canvas of the same strokes."""
