@@ -257,8 +257,15 @@ int canvox_render_host(const canvox_camera* cams, int32_t n_views, float* out_rg
  * library holds until the process exits. The first call on a device looks up
  * that array's device address, so make it before any stream capture. All
  * calls share the array: calls that overlap on the GPU race, so serialise
- * them (one stream, or wait between them). More than 64 views:
- * CANVOX_ERR_INVALID_ARG.
+ * them (one stream, or wait between them). Each call first clears the
+ * array's counters and queue head and stores its view table there with a
+ * small kernel (the table travels as a kernel argument: no host buffer has to
+ * outlive the call). More than 64 views, or n_records / n_leaves above
+ * 2^31 - 1: CANVOX_ERR_INVALID_ARG. Step-limit overruns are not reported:
+ * the limit is the default one (3 * 2^depth + 8 leaves per ray, capped at
+ * 2^31 - 1), and every step crosses one plane of the finest grid that the ray
+ * never crosses again, so a ray visits at most 3 * 2^depth - 2 leaves and
+ * cannot reach the limit below depth 30.
  */
 int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_records, const uint16_t* leaf_rgba_dev,
                           int64_t n_leaves, int32_t depth, double extent, const canvox_camera* cams,

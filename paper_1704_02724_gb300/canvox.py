@@ -11,8 +11,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-# CANVOX_LIB: load the library from another path (for example a build with other compile-time options)
-LIB_PATH = os.environ.get("CANVOX_LIB") or os.path.join(HERE, "libcanvox.so")
+LIB_PATH = os.path.join(HERE, "libcanvox.so")   # the library build() makes, nothing else
 
 OK = 0
 ERR_INVALID_ARG = -1

@@ -7,6 +7,7 @@
 // and keeps its own working memory (counters, ray-queue head, view table and
 // per-view eye paths) in one fixed array in device global memory, declared
 // below. It calls no cudaMalloc, cudaFree or other allocating routine.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -27,8 +28,29 @@ static_assert(kNoallocBytes <= 24576, "the fixed scratch array is 24 KiB");
 // it takes the address from cudaGetSymbolAddress once per device (below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[24576];
 
+// The view table of one call, passed by value as a kernel argument: the set-up kernel
+// copies it into the fixed array, so no host buffer has to outlive the call.
+struct ViewTable {
+    View v[kNoallocMaxViews];
+    int32_t n;
+};
+static_assert(sizeof(ViewTable) <= 32000, "kernel arguments are limited to 32764 bytes");
+
+// Clears the counters, status word and queue head, and stores the view table.
+__global__ void noalloc_setup_kernel(ViewTable t, Scratch* scratch, View* views) {
+    unsigned long long* z = reinterpret_cast<unsigned long long*>(scratch);
+    for (int i = threadIdx.x; i < (int)(sizeof(Scratch) / 8); i += blockDim.x) z[i] = 0ull;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(t.v);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(views);
+    const int words = t.n * (int)(sizeof(View) / 4);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+static_assert(sizeof(Scratch) % 8 == 0 && sizeof(View) % 4 == 0, "word copies");
+
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// Device address of the array per device, looked up once (first call on that device). Atomic, so
+// that first calls from several host threads may race on the lookup without a data race.
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
 
 // Device address of g_noalloc_scratch on the current device (set up on first use).
 int scratch_address(unsigned char** out) {
@@ -36,13 +58,15 @@ int scratch_address(unsigned char** out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(CANVOX_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return set_error(CANVOX_ERR_INVALID_ARG, "device index out of range");
-    if (!g_scratch_addr[dev]) {
+    unsigned char* a = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!a) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return set_error(CANVOX_ERR_CUDA, cudaGetErrorString(e));
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+        a = static_cast<unsigned char*>(p);
+        g_scratch_addr[dev].store(a, std::memory_order_release);  // every thread stores the same address
     }
-    *out = g_scratch_addr[dev];
+    *out = a;
     return CANVOX_OK;
 }
 
@@ -61,6 +85,8 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
         return set_error(CANVOX_ERR_INVALID_ARG, "null pointer or bad count");
     if (n_views > kNoallocMaxViews)
         return set_error(CANVOX_ERR_INVALID_ARG, "canvox_render_noalloc takes at most 64 views per call");
+    if (n_records > 0x7FFFFFFFll || n_leaves > 0x7FFFFFFFll)
+        return set_error(CANVOX_ERR_INVALID_ARG, "pool larger than int32 indices");
     if (depth < 1 || depth > kMaxDepth) return set_error(CANVOX_ERR_INVALID_ARG, "depth not in 1..30");
     if (!(extent > 0.0) || !std::isfinite(extent)) return set_error(CANVOX_ERR_INVALID_ARG, "extent must be finite and > 0");
     {
@@ -68,11 +94,12 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
         const double scaled = std::ldexp(std::frexp(extent, &ex), 23);
         if (scaled != std::floor(scaled)) return set_error(CANVOX_ERR_INVALID_ARG, "extent has more than 23 significant bits");
     }
-    View hv[kNoallocMaxViews];  // host stack, no heap
+    ViewTable vt;  // host stack, no heap; travels as a kernel argument
+    vt.n = n_views;
     int64_t total_rays = 0;
     canvox_render_opts o;
     builtin_render_opts(&o);
-    int rc = build_views(cams, n_views, o.tile_w, hv, &total_rays);
+    int rc = build_views(cams, n_views, o.tile_w, vt.v, &total_rays);
     if (rc) return rc;
     unsigned char* base = nullptr;
     rc = scratch_address(&base);
@@ -87,8 +114,8 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
     View* views = reinterpret_cast<View*>(base + kOffViews);
     EyePath* eye = reinterpret_cast<EyePath*>(base + kOffEye);
     // the array keeps the previous call's contents: the counters and queue head start at zero
-    e = cudaMemsetAsync(scratch, 0, sizeof(Scratch), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(views, hv, sizeof(View) * (size_t)n_views, cudaMemcpyHostToDevice, s);
+    noalloc_setup_kernel<<<1, 256, 0, s>>>(vt, scratch, views);
+    e = cudaGetLastError();
     Tree t;
     t.nodes = node_pool_dev;
     t.ropes = nullptr;

@@ -6,7 +6,8 @@
 * closed forms: homogeneous cube 1 - exp(-sigma L), empty canvas = background;
 * invariants: coarsening, mirror symmetry, embedding at depth 20+ (the
   precision claim of Sec. 6.1-6.3 holds exactly for an FP64 oracle);
-* the camera model: pixel rays recomputed independently.
+* the camera model: pixel rays recomputed independently, and the orthonormalisation of
+  skewed camera frames against a numpy restatement.
 """
 import json
 import math
@@ -19,6 +20,7 @@ import oracle
 import synth
 from synth import random_tree as rt
 from bruteforce import DenseGrid, march
+from camera_cases import gram_schmidt, skewed_cameras
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -212,6 +214,36 @@ def test_camera_pixel_rays():
             dirs.append(f + x * r + y * u)
     ref = oracle.trace_rays(cv, np.tile(eye, (W * H, 1)), np.array(dirs), (0.1, 0.2, 0.3, 1))
     np.testing.assert_allclose(img[5:], ref, rtol=0, atol=1e-12)
+
+
+def test_camera_gram_schmidt_on_skewed_frames():
+    """A non-orthonormal camera renders exactly like its frame orthonormalised by hand in the camera
+    model's order (forward, then up, then right); the other orders give other images (Sec. 6.1:
+    the FP64 eye frame that every pixel ray is built from)."""
+    cv = rt.random_tree(5, seed=72, p_refine=0.55)
+    skew, ortho = skewed_cameras()
+    got = oracle.render(cv, skew)
+    ref = oracle.render(cv, ortho)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+    assert np.mean(np.abs(ref[:, 3]) > 0) > 0.3    # the views see paint
+    # an up-first order, or a right that is only made orthogonal to forward, moves the image: the
+    # pixel rays of those frames (traced as given, not orthonormalised again) differ from the pin
+    for c in skew:
+        W, H, t = int(c["width"]), int(c["height"]), float(c["tan_half_fov_y"])
+        o, n = int(c["out_offset_px"]), W * H
+        u = c["up"] / np.linalg.norm(c["up"])
+        f = c["forward"] - (c["forward"] @ u) * u
+        f /= np.linalg.norm(f)
+        r = c["right"] - (c["right"] @ f) * f - (c["right"] @ u) * u
+        r /= np.linalg.norm(r)
+        f2, u2, _ = gram_schmidt(c["forward"], c["up"], c["right"])
+        r2 = c["right"] - (c["right"] @ f2) * f2
+        r2 /= np.linalg.norm(r2)
+        for fw, uw, rw in ((f, u, r), (f2, u2, r2)):
+            dirs = [fw + ((2 * (i + 0.5) / W - 1) * t * W / H) * rw + ((1 - 2 * (j + 0.5) / H) * t) * uw
+                    for j in range(H) for i in range(W)]
+            bad = oracle.trace_rays(cv, np.tile(c["eye"], (n, 1)), np.array(dirs), tuple(c["background"]))
+            assert np.max(np.abs(bad - ref[o:o + n])) > 1e-3
 
 
 def test_stamp_canvas_matches_bruteforce():

@@ -18,6 +18,7 @@ from paper_1704_02724_gb300 import canvox
 import synth
 from synth import random_tree as rt
 from gpu_util import TOL, config_canvas, max_err, render, upload
+from camera_cases import skewed_cameras
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -84,6 +85,21 @@ def test_random_trees_edge_cameras(seed, depth, extent):
         img, st = render(cv, cams, key=("rt", seed), precision=prec)
         assert np.all(np.isnan(img[~written]))            # nothing outside the views is touched
         assert max_err(img[written], ref[written]) <= tol, prec
+
+
+def test_skewed_camera_frames():
+    """Cameras whose right/up/forward are not orthonormal (scaled, skewed, a right that points left):
+    the library orthonormalises them as the camera model states (forward, then up, then right), so the
+    image matches the oracle and equals, within the bar, the render of the frames orthonormalised by
+    hand (Sec. 6.1: the FP64 eye frame)."""
+    cv = rt.random_tree(6, seed=72, p_refine=0.55, extent=40.0)
+    skew, ortho = skewed_cameras(extent=40.0)
+    ref = oracle.render(cv, skew)
+    for prec, tol in ((cx.PREC_MIXED, TOL), (cx.PREC_FP64, 1e-6)):
+        img, _ = render(cv, skew, key="skew", precision=prec)
+        assert max_err(img, ref) <= tol, prec
+        img_o, _ = render(cv, ortho, key="skew", precision=prec)
+        assert max_err(img, img_o) <= tol, prec
 
 
 def test_t_min_zero_runs_to_canvas_exit():

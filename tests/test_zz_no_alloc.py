@@ -2,12 +2,14 @@
 
 It renders from caller-owned device buffers and keeps its working memory in a
 fixed device array, so it must give the same image as canvox_render, call
-after call (the array keeps the previous call's contents). This file is
-collected last so that a failure here does not hide the other tests.
+after call (the array keeps the previous call's contents), and match the FP64
+oracle like every other render. This file is collected last so that a failure
+here does not hide the other tests.
 """
 import numpy as np
 import pytest
 
+import oracle
 import paper_1704_02724_gb300 as cx
 from paper_1704_02724_gb300 import canvox
 import synth
@@ -38,6 +40,7 @@ def test_noalloc_matches_render_on_two_calls():
     cx.render(cams, ref)
     torch.cuda.synchronize()
     ref = ref.cpu().numpy()
+    ref_oracle = oracle.render(cv, cams)
     # caller-owned device copies of the pools
     nodes = torch.from_numpy(np.ascontiguousarray(cv.nodes)).cuda()
     leaves = torch.from_numpy(np.ascontiguousarray(cv.leaves).view(np.int16)).cuda()
@@ -48,6 +51,7 @@ def test_noalloc_matches_render_on_two_calls():
         img = out.cpu().numpy()
         assert np.all(np.isfinite(img))
         assert float(np.max(np.abs(img.astype(np.float64) - ref))) <= TOL
+        assert float(np.max(np.abs(img.astype(np.float64) - ref_oracle))) <= TOL
 
 
 def test_noalloc_rejects_too_many_views():
@@ -59,3 +63,6 @@ def test_noalloc_rejects_too_many_views():
     with pytest.raises(cx.CanvoxError) as e:
         cx.render_noalloc(nodes, cv.n_records, leaves, cv.n_leaves, cv.depth, cv.extent, cams, out)
     assert e.value.code == canvox.ERR_INVALID_ARG and "64 views" in str(e.value)
+    with pytest.raises(cx.CanvoxError) as e:   # pool sizes beyond int32 indices are refused before any launch
+        cx.render_noalloc(nodes, 2 ** 31, leaves, cv.n_leaves, cv.depth, cv.extent, cams[:1], out)
+    assert e.value.code == canvox.ERR_INVALID_ARG
