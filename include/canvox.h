@@ -101,6 +101,9 @@ typedef struct canvox_camera {
  *   angle_deg     : optional device float per output pixel (CELL32 / WORLD32 / CELL16 only): angle in degrees
  *                   between the initial ray direction and the line from the eye to the ray's final
  *                   position (the ray-angle error of Sec. 6.3).
+ *   count_reads   : 1 = count slot reads, leaf loads and record loads for canvox_stats (mixed precision);
+ *                   0 = leave those three counters at 0 (a few instructions and registers less per leaf
+ *                   step; the image is the same bit for bit).
  */
 typedef struct canvox_render_opts {
     int32_t precision;
@@ -118,6 +121,7 @@ typedef struct canvox_render_opts {
     float err_budget;
     int32_t* step_count;
     float* angle_deg;
+    int32_t count_reads;
 } canvox_render_opts;
 
 /* Counters of the last completed render call (sums over all its rays). */

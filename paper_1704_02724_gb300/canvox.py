@@ -56,6 +56,7 @@ class Opts(ctypes.Structure):
         ("err_budget", ctypes.c_float),
         ("step_count", ctypes.c_void_p),
         ("angle_deg", ctypes.c_void_p),
+        ("count_reads", ctypes.c_int32),
     ]
 
 

@@ -95,6 +95,7 @@ struct MixedParams {
     int32_t frame_levels;
     int32_t smem_records;
     int32_t use_ropes;   // 1: neighbour links (Tree::ropes), 0: stack of ancestors
+    int32_t count_reads; // 1: count slot reads, leaf loads and record loads (canvox_stats)
 };
 
 struct PlainParams {

@@ -148,6 +148,7 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
     p.frame_levels = o.frame_levels;
     p.smem_records = 0;
     p.use_ropes = 0;  // no neighbour links without allocating them
+    p.count_reads = 0;  // these calls report no counters
     e = launch_mixed(p, sms * (bps > 0 ? bps : 1), o.block_threads, s);
     if (e != cudaSuccess) return set_error(CANVOX_ERR_CUDA, cudaGetErrorString(e));
     return CANVOX_OK;

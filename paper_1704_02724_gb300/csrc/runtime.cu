@@ -118,6 +118,7 @@ void builtin_defaults(canvox_render_opts* o) {
     o->err_budget = 3.0e-6f;
     o->step_count = nullptr;
     o->angle_deg = nullptr;
+    o->count_reads = 1;
 }
 
 int ensure_device() {
@@ -249,6 +250,7 @@ int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (o->tile_w != 4 && o->tile_w != 8 && o->tile_w != 16 && o->tile_w != 32)
         return fail(CANVOX_ERR_INVALID_ARG, "tile_w %d (4, 8, 16 or 32)", o->tile_w);
     if (o->traversal != 0 && o->traversal != 1) return fail(CANVOX_ERR_INVALID_ARG, "traversal %d (0 or 1)", o->traversal);
+    if (o->count_reads != 0 && o->count_reads != 1) return fail(CANVOX_ERR_INVALID_ARG, "count_reads %d (0 or 1)", o->count_reads);
     if (!(o->err_budget >= 0.0f) || !std::isfinite(o->err_budget)) return fail(CANVOX_ERR_INVALID_ARG, "err_budget");
     if (!std::isfinite(o->t_min)) return fail(CANVOX_ERR_INVALID_ARG, "t_min");
     if (o->t_min < 0.0f) o->t_min = 9.5367431640625e-07f;  // 2^-20
@@ -300,6 +302,7 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
         p.refill = o.refill;
         p.smem_records = o.smem_records;
         p.use_ropes = o.traversal == 0 ? 1 : 0;
+        p.count_reads = o.count_reads;
         if (!o.per_view) {
             p.views = g.d_views;
             p.eye = g.d_eye;

@@ -22,18 +22,26 @@
 // paper's cell-local frame (origin at a cell, unit size) widened from one cell
 // to a subtree. The frame is re-anchored in FP64 whenever the ray leaves it, so
 // the drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames.
-// Inside a frame every crossing time is a double-float: an unevaluated sum
+// inv_d and nod_f are each kept as two FP32 words. Decisions (which face of the
+// leaf the ray leaves by, which side of a mid-plane it is on) are screened in
+// plain FP32 with a proven margin, and taken in FP64 from the exact planes when
+// the screen cannot decide (the ray passes within about 2^-22 frame units of an
+// edge or a plane: a few steps in a hundred thousand). The time of the exit
+// face, which sets the segment length, is a double-float: an unevaluated sum
 // hi + lo of two FP32 words formed with error-free transformations (Dekker's
 // product by fma, Knuth's two-sum), good to about 2^-44 |inv_d| frame units.
-// Decisions closer than that bound (exit axis near an edge, child choice near
-// a mid-plane) are retaken in FP64 from exact planes: t = P inv_d + nod.
 // A boundary between leaves of different value moves the pixel by at most
 // 2 T max(sigma) |dt|; each ray carries a budget for these bounds, and a
 // boundary whose bound would exceed it is recomputed in FP64.
 //
 // Compositing (emission-absorption reading of Sec. 6.2): per segment of signed
 // length l in a leaf (sigma, rgb): a = 1 - exp(-sigma l), C += T a rgb,
-// tau += sigma l, T = exp(-tau), with compensated (Kahan) FP32 sums for C, tau.
+// T *= 1 - a, with a compensated (Kahan) FP32 sum for C and the transmittance
+// kept as a running product (one rounding per leaf, unbiased).
+//
+// The per-lane counters of slot reads, leaf loads and record loads (the
+// algorithmic bytes of a render) are a template option: a render that does
+// not report them runs without them.
 #include <cuda_fp16.h>
 
 #include "canvox_internal.cuh"
@@ -45,6 +53,12 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr float kEpsDF = 5.684341886080802e-14f;   // 2^-44: double-float crossing-time bound per |inv_d|
 constexpr float kEpsDF2 = 1.1368683772161603e-13f; // 2^-43 = 2 * 2^-44: factor 2 of the colour bound
 constexpr int kMaxFrameBits = 22;                   // a frame spans at most 22 levels (exact FP32 planes)
+constexpr float kEps21 = 4.76837158203125e-07f;     // 2^-21
+constexpr float kEps22 = 2.384185791015625e-07f;    // 2^-22
+constexpr float kEps41 = 4.547473508864641e-13f;    // 2^-41
+constexpr float kBigF = 1.0e37f;                    // stands for the time of a face the ray never meets (d_a = 0)
+constexpr float kEps42 = 2.2737367544323206e-13f;   // 2^-42
+constexpr float kOneMinus20 = 0.99999904632568359f; // 1 - 2^-20
 
 // Resident 256-thread blocks per SM the register allocation must allow (occupancy knob).
 #ifndef CANVOX_MIN_BLOCKS
@@ -62,14 +76,10 @@ __device__ __forceinline__ float hhi(unsigned w) { return half_bits_to_float(w >
 __device__ __forceinline__ float small_uint_to_float(uint32_t x) {
     return __fsub_rn(__int_as_float((int)(0x4B000000u | x)), 8388608.0f);
 }
-__device__ __forceinline__ float finf() { return __int_as_float(0x7F800000); }
 
 // x[a] for a runtime axis without indexing an array (which would put it in local memory).
 template <typename V>
 __device__ __forceinline__ V pick(int a, V x0, V x1, V x2) { return a == 0 ? x0 : (a == 1 ? x1 : x2); }
-
-// (ah, al) < (bh, bl) for normalised double-floats.
-__device__ __forceinline__ bool df_less(float ah, float al, float bh, float bl) { return ah < bh || (ah == bh && al < bl); }
 
 extern __shared__ int32_t s_nodes[];  // copy of the tree's first records (kernel instance with kSmem)
 
@@ -102,11 +112,6 @@ __device__ __forceinline__ void df_cross(float P, float ih, float il, float nh, 
     lo = __fsub_rn(t, __fsub_rn(hi, s));
 }
 
-// (ah + al) - (bh + bl), rounded to FP32.
-__device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl) {
-    return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
-}
-
 constexpr int kBlock = 256;
 
 // FP64 state, output address and rare counters of a lane: read only by rebases,
@@ -126,8 +131,10 @@ struct Ray {
     float ih[3], il[3];         // inv_d as two FP32 words (0 for d = 0)
     float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
     float sf, sf_eps;           // frame size, frame size * 2^-43
+    float gscr;                 // 2^-41 max_a (|ih_a| + |nh_a|): double-float part of the exit screen's margin
     float cur_hi, cur_lo;       // frame-local parameter of the current leaf's entry
-    float* acc;  // shared, stride kBlock: C0, C1, C2 (colour), k0, k1, k2 (their Kahan terms), tau, ktau, err
+    float2* acc;  // shared, stride kBlock: (sum, Kahan term) of the colour channels 0, 1, 2
+    float* err;   // shared: colour-error bound spent so far (the budget of the FP32 boundaries)
     float T;
     uint32_t c[3];
     int32_t L, f;
@@ -142,6 +149,7 @@ struct Ray {
 
 __device__ __forceinline__ bool is_zero(const Ray& r, int a) { return (r.zmask >> a) & 1u; }
 #define ACC(r, i) ((r).acc[(i) * kBlock])
+#define ERR(r) (*(r).err)
 
 // Ray on the high side of the global plane x_a = M just after parameter t (FP64).
 __device__ __forceinline__ uint32_t high64(const Ray& r, int a, double M, double t) {
@@ -162,19 +170,54 @@ __device__ __forceinline__ void split_local(const Ray& r, double t, float& hi, f
     lo = (float)(tl - (double)hi);
 }
 
+// Exit face of the level-L leaf c by the FP64 crossing times of its exact far planes (ties to the lowest
+// axis), and that time as a frame-local double-float. Taken on a few leaf steps in a hundred thousand (a
+// ray within about 2^-22 frame units of an edge), so it is kept out of line: its FP64 code then does not
+// weigh on the register allocation of the step loop.
+struct Exit64 {
+    double t;
+    float hi, lo;
+    int ax;
+};
+__device__ __noinline__ Exit64 exit_face64(Cold* k, uint32_t zmask, uint32_t dpos, uint32_t c0, uint32_t c1, uint32_t c2,
+                                           int L, double extent, double half) {
+    Exit64 e;
+    e.t = __longlong_as_double(0x7FF0000000000000ll);
+    e.ax = 0;
+    const double w = extent * pow2d(-L);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((zmask >> a) & 1u) continue;
+        const uint32_t cs = (a == 0 ? c0 : (a == 1 ? c1 : c2)) + ((dpos >> a) & 1u);
+        const double ta = fma(fma((double)cs, w, -half), k->inv64[a], k->nod64[a]);
+        if (ta < e.t) {
+            e.t = ta;
+            e.ax = a;
+        }
+    }
+    const double tl = (e.t - k->tf) * k->invS;
+    e.hi = (float)tl;
+    e.lo = (float)(tl - (double)e.hi);
+    k->n_f64 += 1;
+    return e;
+}
+
 // Enter the frame at level r.f that holds the cell (r.L, r.c); t = FP64 parameter of the entry.
 __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_extent, double t) {
     r.k->tf = t;
     const int sh = r.L - r.f;
     const double Sf = T.extent * pow2d(-r.f);
     r.k->invS = pow2d(r.f) * inv_extent;
+    float g = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double Fmin = fma((double)(r.c[a] >> sh), Sf, -T.half);
         const double n = is_zero(r, a) ? (r.k->nod64[a] - Fmin) * r.k->invS : (fma(Fmin, r.k->inv64[a], r.k->nod64[a]) - t) * r.k->invS;
         r.nh[a] = (float)n;
         r.nl[a] = (float)(n - (double)r.nh[a]);
+        g = fmaxf(g, __fadd_rn(fabsf(r.ih[a]), fabsf(r.nh[a])));
     }
+    r.gscr = __fmul_rn(kEps41, g);
     r.sf = (float)Sf;
     r.sf_eps = r.sf * kEpsDF2;
     r.cur_hi = 0.0f;
@@ -186,27 +229,31 @@ __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_exte
 // zero: a boundary can land slightly before the cursor (within its error
 // bound), and only the signed lengths of consecutive segments telescope, so a
 // boundary between two leaves of equal value then costs nothing.
+__device__ __forceinline__ void kahan_add2(float2& sc, float x) { kahan_add(sc.x, sc.y, x); }
+
 __device__ __forceinline__ void composite(Ray& r, float teh, float tel) {
     const float ell = ((teh - r.cur_hi) + (tel - r.cur_lo)) * r.sf;
     if (r.val.y >> 16) {
         const float s = hsig(r.val);
-        const float x = s * ell;
-        const float a = -expm1f(-x);
-        const float w = r.T * a;
-        kahan_add(ACC(r, 0), ACC(r, 3), w * hlo(r.val.x));
-        kahan_add(ACC(r, 1), ACC(r, 4), w * hhi(r.val.x));
-        kahan_add(ACC(r, 2), ACC(r, 5), w * hlo(r.val.y));
-        kahan_add(ACC(r, 6), ACC(r, 7), x);
-        r.T = expf(-ACC(r, 6));
+        const float em = expm1f(-s * ell);  // -a
+        const float w = -r.T * em;
+        float2 c0 = ACC(r, 0), c1 = ACC(r, 1), c2 = ACC(r, 2);
+        kahan_add2(c0, w * hlo(r.val.x));
+        kahan_add2(c1, w * hhi(r.val.x));
+        kahan_add2(c2, w * hlo(r.val.y));
+        ACC(r, 0) = c0;
+        ACC(r, 1) = c1;
+        ACC(r, 2) = c2;
+        r.T = __fmaf_rn(r.T, em, r.T);  // T (1 - a)
     }
 }
 
 __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
     const View& V = P.views[r.k->view];
     float4 o;
-    o.x = ACC(r, 0) + r.T * V.bg[0];
-    o.y = ACC(r, 1) + r.T * V.bg[1];
-    o.z = ACC(r, 2) + r.T * V.bg[2];
+    o.x = ACC(r, 0).x + r.T * V.bg[0];
+    o.y = ACC(r, 1).x + r.T * V.bg[1];
+    o.z = ACC(r, 2).x + r.T * V.bg[2];
     o.w = 1.0f - r.T;
     const int64_t pix = V.out_offset + (int64_t)r.k->pix;
     P.out[pix] = o;
@@ -216,8 +263,14 @@ __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
 }
 
 // Child bit on axis a of the cell at level `lev` with coordinate cc, for the ray
-// just after the frame-local time (th, tl). Double-float with an ambiguity
-// margin (margin_t: the bound of (th, tl) itself), else FP64 at need64().
+// just after the frame-local time (th, tl) (a double-float whose own error is
+// at most margin_t). Screened in plain FP32: the mid-plane time
+//     F = fl(fl(Mp ih + nh) + fl(Mp il + nl))        (Mp <= 1: a frame plane)
+// is within 2^-23 |F| + 2^-47 (|ih| + |nh|) of the exact time, and the
+// difference D = fl(fl(F - th) - tl) within 2^-23 (|F| + |th| + |D|) more.
+// When |D| exceeds 2^-21 (|F| + |th|) + 2^-42 (|ih| + |nh|) + margin_t (with
+// room for its own rounding) the side is the sign of D; otherwise, and for
+// frames deeper than 22 levels, the side is decided in FP64 at need64().
 template <typename Need64>
 __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a, uint32_t cc, int lev, float th,
                                               float tl, float margin_t, Need64 need64) {
@@ -228,10 +281,11 @@ __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a
             const float dm = __fadd_rn(__fsub_rn(r.nh[a], Mp), r.nl[a]);
             if (fabsf(dm) > kEpsDF) return dm >= 0.0f;
         } else {
-            float mh, ml;
-            df_cross(Mp, r.ih[a], r.il[a], r.nh[a], r.nl[a], mh, ml);
-            const float dm = df_diff(mh, ml, th, tl);
-            if (fabsf(dm) > kEpsDF * fabsf(r.ih[a]) + margin_t) return r.ih[a] > 0.0f ? (dm <= 0.0f) : (dm > 0.0f);
+            const float F = __fadd_rn(__fmaf_rn(Mp, r.ih[a], r.nh[a]), __fmaf_rn(Mp, r.il[a], r.nl[a]));
+            const float D = __fsub_rn(__fsub_rn(F, th), tl);
+            const float screen = __fmaf_rn(kEps21, __fadd_rn(fabsf(F), fabsf(th)),
+                                           __fmaf_rn(kEps42, __fadd_rn(fabsf(r.ih[a]), fabsf(r.nh[a])), margin_t));
+            if (fabsf(D) * kOneMinus20 > screen) return r.ih[a] > 0.0f ? (D <= 0.0f) : (D > 0.0f);
         }
     }
     const double t64 = need64();
@@ -240,7 +294,7 @@ __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a
 }
 
 // Start ray g of the launch. Returns true if it has a leaf to step from.
-template <bool kSmem, bool kRopes>
+template <bool kSmem, bool kRopes, bool kCount>
 __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsigned long long g, int32_t* stk) {
     const Tree& T = P.tree;
     g += (unsigned long long)P.ray_base;
@@ -261,10 +315,9 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     if (i >= V.width || j >= V.height) return false;  // padding lane of a ragged tile
     r.k->view = lo;
     r.k->pix = (uint32_t)j * (uint32_t)V.width + (uint32_t)i;
-    ACC(r, 0) = ACC(r, 1) = ACC(r, 2) = ACC(r, 3) = ACC(r, 4) = ACC(r, 5) = 0.0f;
-    ACC(r, 6) = ACC(r, 7) = 0.0f;
+    ACC(r, 0) = ACC(r, 1) = ACC(r, 2) = make_float2(0.0f, 0.0f);
     r.T = 1.0f;
-    ACC(r, 8) = 0.0f;
+    ERR(r) = 0.0f;
     r.steps = 0;
     // pixel-centre ray in FP64 (Sec. 6.1)
     double d[3];
@@ -314,8 +367,8 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         r.c[1] = E.c[1];
         r.c[2] = E.c[2];
         r.val = E.val;
-        r.n_reads += r.L;
-        r.n_leaf += (uint32_t)E.stored;
+        if (kCount) r.n_reads += r.L;
+        if (kCount) r.n_leaf += (uint32_t)E.stored;
         r.steps = 1;
         r.f = max(0, r.L - P.frame_levels);
         set_frame(r, T, inv_extent, t0);
@@ -346,7 +399,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
             k |= (int)b << a;
         }
         slot = load_slot<kSmem>(T, P.smem_records, rec, k);
-        r.n_rec += 1;
+        if (kCount) r.n_rec += 1;
         if (slot > 0) {
             ++lev;
             if (!kRopes) stk[lev] = slot;
@@ -358,10 +411,10 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         }
     }
     r.L = lev + 1;
-    r.n_reads += r.L;
+    if (kCount) r.n_reads += r.L;
     if (slot < 0) {
         r.val = load_leaf(T, slot);
-        r.n_leaf += 1;
+        if (kCount) r.n_leaf += 1;
     } else {
         r.val = make_uint2(0u, 0u);
     }
@@ -374,61 +427,50 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
 }
 
 // One leaf step. Returns false once the ray is finished (its pixel written).
-template <bool kSmem, bool kRopes>
+template <bool kSmem, bool kRopes, bool kCount>
 __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_t* stk) {
     const Tree& T = P.tree;
-    // 1. exit of the current leaf: double-float crossing times in the frame
+    // 1. exit of the current leaf: the far face on each axis is the plane P_a (frame units, exact)
     const int kf = r.L - r.f;
     const float sc = pow2f(-kf);
     const uint32_t fmask = (1u << kf) - 1u;
-    float th0, tl0, th1, tl1, th2, tl2;
-#define CANVOX_EXIT_T(a, H, L_)                                                                    \
-    if (is_zero(r, a)) {                                                                           \
-        H = finf();                                                                                \
-        L_ = 0.0f;                                                                                 \
-    } else {                                                                                       \
-        const uint32_t rel = (r.c[a] & fmask) + ((r.dpos >> (a)) & 1u);                            \
-        df_cross(small_uint_to_float(rel) * sc, r.ih[a], r.il[a], r.nh[a], r.nl[a], H, L_);          \
-    }
-    CANVOX_EXIT_T(0, th0, tl0)
-    CANVOX_EXIT_T(1, th1, tl1)
-    CANVOX_EXIT_T(2, th2, tl2)
-#undef CANVOX_EXIT_T
-    // exit axis: smallest time, ties to the lowest axis; and the runner-up
-    int ax = 0;
-    float teh = th0, tel = tl0;
-    if (df_less(th1, tl1, teh, tel)) { ax = 1; teh = th1; tel = tl1; }
-    if (df_less(th2, tl2, teh, tel)) { ax = 2; teh = th2; tel = tl2; }
-    float sh2, sl2;
-    int a2;
-    {
-        const float ph = ax == 0 ? th1 : th0, pl = ax == 0 ? tl1 : tl0;
-        const float qh = ax == 2 ? th1 : th2, ql = ax == 2 ? tl1 : tl2;
-        const int pa = ax == 0 ? 1 : 0, qa = ax == 2 ? 1 : 2;
-        const bool q = df_less(qh, ql, ph, pl);
-        sh2 = q ? qh : ph;
-        sl2 = q ? ql : pl;
-        a2 = q ? qa : pa;
-    }
-    float inv_ax = pick(ax, r.ih[0], r.ih[1], r.ih[2]);
+    const float P0 = small_uint_to_float((r.c[0] & fmask) + (r.dpos & 1u)) * sc;
+    const float P1 = small_uint_to_float((r.c[1] & fmask) + ((r.dpos >> 1) & 1u)) * sc;
+    const float P2 = small_uint_to_float((r.c[2] & fmask) + ((r.dpos >> 2) & 1u)) * sc;
+    // FP32 screen: F_a = fl(fl(P_a ih + nh) + fl(P_a il + nl)) is within 2^-23 |F_a| + 2^-47 (|ih| + |nh|)
+    // of the exact crossing time. When the runner-up F_s exceeds the smallest F_b by more than
+    // 2^-22 (|F_s| + |F_b|) + 2^-41 max_a (|ih_a| + |nh_a|) (the frame's gscr), F_b's face is the exit face,
+    // at least 2^-44 (|ih_b| + |ih_s|) ahead of the others in double-float time: only its double-float
+    // time is formed. Otherwise (the ray passes within about 2^-22 frame units of an edge of the leaf) the
+    // face is chosen in FP64 from the exact planes.
+    float teh, tel, inv_ax;
+    int ax;
     bool have64 = false;
     double te64 = 0.0;
-    if (df_diff(sh2, sl2, teh, tel) <= kEpsDF * (fabsf(inv_ax) + fabsf(pick(a2, r.ih[0], r.ih[1], r.ih[2])))) {
-        // the exit face is ambiguous (ray within the bound of an edge): decide in FP64
-        double best = __longlong_as_double(0x7FF0000000000000ll);
-        int bax = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (is_zero(r, a)) continue;
-            const double ta = face_t64(r, T, a, r.c[a] + ((r.dpos >> a) & 1u), r.L);
-            if (ta < best) { best = ta; bax = a; }
+    {
+        const float F0 = is_zero(r, 0) ? kBigF : __fadd_rn(__fmaf_rn(P0, r.ih[0], r.nh[0]), __fmaf_rn(P0, r.il[0], r.nl[0]));
+        const float F1 = is_zero(r, 1) ? kBigF : __fadd_rn(__fmaf_rn(P1, r.ih[1], r.nh[1]), __fmaf_rn(P1, r.il[1], r.nl[1]));
+        const float F2 = is_zero(r, 2) ? kBigF : __fadd_rn(__fmaf_rn(P2, r.ih[2], r.nh[2]), __fmaf_rn(P2, r.il[2], r.nl[2]));
+        ax = 0;
+        float Fb = F0;
+        if (F1 < Fb) { ax = 1; Fb = F1; }
+        if (F2 < Fb) { ax = 2; Fb = F2; }
+        const float Fs = fmaxf(fminf(F0, F1), fminf(fmaxf(F0, F1), F2));  // the median: runner-up
+        const bool clear = __fsub_rn(Fs, Fb) > __fmaf_rn(kEps22, __fadd_rn(fabsf(Fs), fabsf(Fb)), r.gscr);
+        if (clear) {
+            inv_ax = pick(ax, r.ih[0], r.ih[1], r.ih[2]);
+            df_cross(pick(ax, P0, P1, P2), inv_ax, pick(ax, r.il[0], r.il[1], r.il[2]), pick(ax, r.nh[0], r.nh[1], r.nh[2]),
+                     pick(ax, r.nl[0], r.nl[1], r.nl[2]), teh, tel);
+        } else {
+            // near an edge: the smallest FP64 crossing time of the exact far planes, ties to the lowest axis
+            const Exit64 e = exit_face64(r.k, r.zmask, r.dpos, r.c[0], r.c[1], r.c[2], r.L, T.extent, T.half);
+            ax = e.ax;
+            inv_ax = pick(ax, r.ih[0], r.ih[1], r.ih[2]);
+            te64 = e.t;
+            teh = e.hi;
+            tel = e.lo;
+            have64 = true;
         }
-        ax = bax;
-        inv_ax = pick(ax, r.ih[0], r.ih[1], r.ih[2]);
-        te64 = best;
-        have64 = true;
-        split_local(r, te64, teh, tel);
-        r.k->n_f64 += 1;
     }
     // 2. neighbour across the exit face
     const uint32_t up = (r.dpos >> ax) & 1u;
@@ -448,8 +490,8 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         // leaving the canvas: last segment, bounded like a boundary to sigma = 0
         if (!have64 && (r.val.y >> 16)) {
             const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(inv_ax);
-            if (ACC(r, 8) + need > P.err_budget) need64();
-            else ACC(r, 8) += need;
+            if (ERR(r) + need > P.err_budget) need64();
+            else ERR(r) += need;
         }
         composite(r, teh, tel);
         finish(r, P);
@@ -472,7 +514,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             lv = r.L;
         } else {
             const uint2 rp = __ldg(T.ropes + (int64_t)r.pr * 6 + 2 * ax + (int)up);
-            r.n_rec += 1;
+            if (kCount) r.n_rec += 1;
             prec = (int32_t)rp.x;
             kk = (int)((rp.y >> 8) & 7u);
             lv = (int)(rp.y & 255u);
@@ -484,7 +526,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         kk = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
     }
     int32_t slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
-    r.n_rec += 1;
+    if (kCount) r.n_rec += 1;
     const float margin_ax = kEpsDF * fabsf(inv_ax);
     while (slot > 0) {
         // internal cell at level lv (record `slot`): choose its child at level lv + 1
@@ -516,15 +558,15 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         kk = k;
         ++lv;
         slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
-        r.n_rec += 1;
+        if (kCount) r.n_rec += 1;
     }
     const int lev = lv - 1;
     const int Ln = lev + 1;
-    r.n_reads += (uint32_t)(Ln - lstar);
+    if (kCount) r.n_reads += (uint32_t)(Ln - lstar);
     uint2 nval = make_uint2(0u, 0u);
     if (slot < 0) {
         nval = load_leaf(T, slot);
-        r.n_leaf += 1;
+        if (kCount) r.n_leaf += 1;
     }
     const bool rebase = fexit || (Ln - r.f > P.frame_levels);
     // 4. precision of this boundary
@@ -533,8 +575,8 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             need64();
         } else if (nval.x != r.val.x || nval.y != r.val.y) {
             const float need = r.T * fmaxf(hsig(r.val), hsig(nval)) * r.sf_eps * fabsf(inv_ax);
-            if (ACC(r, 8) + need > P.err_budget) need64();
-            else ACC(r, 8) += need;
+            if (ERR(r) + need > P.err_budget) need64();
+            else ERR(r) += need;
         }
     }
     // 5. composite the current leaf, then terminate or advance
@@ -576,10 +618,11 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-template <bool kSmem, bool kRopes>
+template <bool kSmem, bool kRopes, bool kCount>
 __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedParams P) {
     __shared__ Cold cold[kBlock];
-    __shared__ float accs[9 * kBlock];
+    __shared__ float2 accs[3 * kBlock];
+    __shared__ float errs[kBlock];
     if (kSmem) {
         for (int i = threadIdx.x; i < P.smem_records * 8; i += blockDim.x) s_nodes[i] = __ldg(P.tree.nodes + i);
         __syncthreads();
@@ -588,6 +631,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
     Ray r;
     r.k = &cold[threadIdx.x];
     r.acc = &accs[threadIdx.x];
+    r.err = &errs[threadIdx.x];
     r.k->n_rays = r.k->n_steps = r.k->n_f64 = r.k->n_rebase = 0;
     r.n_reads = r.n_leaf = r.n_rec = 0;
     const double inv_extent = 1.0 / P.tree.extent;
@@ -604,7 +648,7 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
             if (base + __popc(idle) >= (unsigned long long)P.total_rays) drained = true;
             if (!alive) {
                 const unsigned long long g = base + __popc(idle & ((1u << lane) - 1u));
-                if (g < (unsigned long long)P.total_rays) alive = ray_init<kSmem, kRopes>(r, P, inv_extent, g, stk);
+                if (g < (unsigned long long)P.total_rays) alive = ray_init<kSmem, kRopes, kCount>(r, P, inv_extent, g, stk);
             }
             busy = __ballot_sync(kFull, alive);
             if (!drained && __popc(busy) <= P.refill) continue;
@@ -614,11 +658,12 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
             continue;
         }
         do {
-            if (alive) alive = ray_step<kSmem, kRopes>(r, P, inv_extent, stk);
+            if (alive) alive = ray_step<kSmem, kRopes, kCount>(r, P, inv_extent, stk);
             busy = __ballot_sync(kFull, alive);
         } while (busy != 0u && (drained || __popc(busy) > P.refill));
     }
-    const unsigned long long v[7] = {r.k->n_rays, r.k->n_steps, r.n_reads, r.n_leaf, r.n_rec, r.k->n_f64, r.k->n_rebase};
+    const unsigned long long v[7] = {r.k->n_rays, r.k->n_steps, kCount ? r.n_reads : 0u, kCount ? r.n_leaf : 0u,
+                                     kCount ? r.n_rec : 0u, r.k->n_f64, r.k->n_rebase};
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         const unsigned long long s = warp_sum(v[i]);
@@ -628,32 +673,38 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
 
 }  // namespace
 
-template <bool kRopes>
+template <bool kRopes, bool kCount>
 cudaError_t launch_mixed_t(const MixedParams& p, int grid, int block, cudaStream_t s) {
     if (p.smem_records <= 0) {
-        mixed_kernel<false, kRopes><<<grid, block, 0, s>>>(p);
+        mixed_kernel<false, kRopes, kCount><<<grid, block, 0, s>>>(p);
         return cudaGetLastError();
     }
     // static (per-lane records) plus dynamic shared memory passes the 48 KB default: always opt in
     const int smem = p.smem_records * 32;
-    const cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true, kRopes>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const cudaError_t e =
+        cudaFuncSetAttribute(mixed_kernel<true, kRopes, kCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    mixed_kernel<true, kRopes><<<grid, block, smem, s>>>(p);
+    mixed_kernel<true, kRopes, kCount><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s) {
-    return (p.use_ropes && p.tree.ropes) ? launch_mixed_t<true>(p, grid, block, s) : launch_mixed_t<false>(p, grid, block, s);
+    const bool ropes = p.use_ropes && p.tree.ropes;
+    if (p.count_reads)
+        return ropes ? launch_mixed_t<true, true>(p, grid, block, s) : launch_mixed_t<false, true>(p, grid, block, s);
+    return ropes ? launch_mixed_t<true, false>(p, grid, block, s) : launch_mixed_t<false, false>(p, grid, block, s);
 }
 
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out) {
-    // all four instances share the register and static shared-memory budget
-    if (smem_bytes <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<false, true>, block, 0);
-    cudaError_t e = cudaFuncSetAttribute(mixed_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mixed_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    // all instances share the register and static shared-memory budget
+    if (smem_bytes <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<false, true, true>, block, 0);
+    cudaError_t e = cudaSuccess;
+    const void* fns[4] = {(const void*)mixed_kernel<true, true, true>, (const void*)mixed_kernel<true, false, true>,
+                          (const void*)mixed_kernel<true, true, false>, (const void*)mixed_kernel<true, false, false>};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<true, true>, block, smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, mixed_kernel<true, true, true>, block, smem_bytes);
 }
 
 }  // namespace canvox
