@@ -71,11 +71,12 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(cid, res_scale, n_fine):
-    """DRAM bytes per launch of the traversal kernel from the committed ncu summary, or None when the
-    summary is for another workload or the kernel source has changed since it was captured."""
+def profiled_counters(cid, res_scale, n_fine):
+    """Per-launch hardware counters of the traversal kernel from the committed ncu summary (DRAM bytes, L2
+    bytes, warp and thread instructions), or None when the summary is for another workload or the kernel
+    source has changed since it was captured."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "mixed_kernel_c2_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "mixed_kernel_c2_counters.txt")
     if cid != 2 or res_scale != 1.0 or n_fine or not os.path.exists(p):
         return None
     src = os.path.join(ROOT, "paper_1704_02724_gb300", "csrc", "trace_mixed.cu")
@@ -89,7 +90,8 @@ def profiled_traffic(cid, res_scale, n_fine):
                 fields[k.strip()] = v.strip()
     if fields.get("kernel_sha256") != sha:
         return None
-    return float(fields["dram_bytes_per_launch"])
+    return {k: float(fields[k]) for k in ("dram_bytes_per_launch", "lts_bytes_per_launch", "warp_inst_per_launch",
+                                          "thread_inst_per_launch", "steps_per_launch")}
 
 
 class Clocks:
@@ -333,7 +335,28 @@ def main():
         peak, peak_kind = measured_peaks()
         algo_bytes = 32 * stats["slot_reads"] + 8 * stats["leaf_loads"] + 16 * stats["rays"]
         achieved = algo_bytes / (ms_step * 1e-3) / 1e9
-        traffic = profiled_traffic(cid, args.res_scale, args.n_fine)
+        ctr = profiled_counters(cid, args.res_scale, args.n_fine)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        issue_peak = n_sm * 4 * clk_mhz * 1e6 / 1e9   # warp instructions per second, G: one per scheduler per cycle
+        roofline = {
+            # the bytes roof of the formula: algorithmic bytes per launch over the measured HBM copy bandwidth
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ctr["dram_bytes_per_launch"] if ctr else None, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": algo_bytes, "bytes_formula": "32*slot_reads + 8*leaf_loads + 16*rays",
+            "bound_note": "what binds is instruction issue (ncu: ~71 % of issue slots busy, ALU the busiest pipe, "
+                          "DRAM ~0.2 % of the algorithmic bytes): see 'issue'; the gathers are served by L1/L2",
+        }
+        if ctr:
+            # counters of this launch from the committed ncu capture (same kernel source, same schedule)
+            roofline["issue"] = {
+                "achieved": ctr["warp_inst_per_launch"] / (ms_step * 1e-3) / 1e9, "peak": issue_peak,
+                "unit": "G warp-instructions/s", "frac": ctr["warp_inst_per_launch"] / (ms_step * 1e-3) / 1e9 / issue_peak,
+                "peak_kind": f"derived: {n_sm} SMs x 4 schedulers x 1 warp-instruction/cycle x {clk_mhz:.0f} MHz (sampled)",
+                "thread_inst_per_leaf_step": ctr["thread_inst_per_launch"] / ctr["steps_per_launch"],
+                "warp_inst_per_leaf_step": ctr["warp_inst_per_launch"] / ctr["steps_per_launch"]}
+            roofline["l2"] = {"achieved": ctr["lts_bytes_per_launch"] / (ms_step * 1e-3) / 1e9, "unit": "GB/s",
+                              "note": "lts__t_bytes per launch (ncu) over the timed launch; see l2_gather for the probe"}
         line = {
             "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -349,12 +372,7 @@ def main():
             "wall_ms_per_step_incl_flush": wall * 1e3 / args.steps,
             # per render: the eye-path kernel and the traversal kernel (one per view in per-view mode)
             "gpu_launches": args.steps * (1 + (1 if not opts.get("per_view") else len(cams))),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": algo_bytes,
-                         "note": "gathers are L1/L2-resident: DRAM traffic is ~0.2 % of the algorithmic bytes;"
-                                 " the kernel is issue/latency-bound (profiles/)",
-                         "bytes_formula": "32*slot_reads + 8*leaf_loads + 16*rays"},
+            "roofline": roofline,
             "stats": {k: v for k, v in stats.items() if k != "status"},
             "hash_ok": h_hash == d_hash,
             "autotune": tuned,
@@ -377,6 +395,22 @@ def main():
         ms64 = statistics.median(f64)
         line["fp64_plain"] = {"value": rays / (ms64 * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms64,
                               "speedup_of_mixed": ms64 / ms_step}
+        # the FP64 twin of the mixed traversal (same links, queue and schedule; FP64 arithmetic): what the
+        # precision scheme alone buys
+        out64l = torch.empty_like(out)
+        cx.render(cams, out64l, precision=cx.PREC_FP64_LINKS, count_reads=0)
+        torch.cuda.synchronize()
+        f64l = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            cx.render(cams, out64l, precision=cx.PREC_FP64_LINKS, count_reads=0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f64l.append(e0.elapsed_time(e1))
+        ms64l = statistics.median(f64l)
+        line["fp64_links"] = {"value": rays / (ms64l * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms64l,
+                              "speedup_of_mixed": ms64l / ms_step}
         out32 = torch.empty_like(out)
         cx.render(cams, out32, precision=cx.PREC_FP32)
         torch.cuda.synchronize()
@@ -408,14 +442,19 @@ def main():
         # measurement helpers: L2 sector-gather and FP64 probes, the frame's footprint (compulsory bytes)
         l2_gbs = cx.probe_l2_gather()
         line["l2_gather"] = {"probe_gbs": l2_gbs, "achieved_gbs": achieved, "frac": achieved / l2_gbs,
-                             "note": "random 32 B sector gathers from a half-L2 buffer, L1 bypassed"}
+                             "note": "algorithmic bytes against random 32 B sector gathers from a half-L2 buffer,"
+                                     " L1 bypassed"}
+        if "l2" in line["roofline"]:
+            line["roofline"]["l2"]["probe_gbs"] = l2_gbs
+            line["roofline"]["l2"]["frac"] = line["roofline"]["l2"]["achieved"] / l2_gbs
         line["fp64_probe_gflops"] = cx.probe_fp64()
         t_fp = time.perf_counter()
         n_rec_fp, n_leaf_fp = cx.footprint(cams)
         line["footprint"] = {"records": n_rec_fp, "leaves": n_leaf_fp,
                              "compulsory_bytes": 32 * n_rec_fp + 8 * n_leaf_fp,
                              "with_links_bytes": 80 * n_rec_fp + 8 * n_leaf_fp,
-                             "dram_bytes_per_launch": traffic, "seconds": round(time.perf_counter() - t_fp, 1)}
+                             "dram_bytes_per_launch": line["roofline"]["traffic"],
+                             "seconds": round(time.perf_counter() - t_fp, 1)}
         # FP64 oracle on host cores: CPU baseline and the error of each GPU path on its sample
         px, ref, rate, wall_s, cores, counts = oracle_rate(canvas, cams, args.cpu_seconds)
         img = out.cpu().numpy().astype(np.float64)[px]
@@ -425,6 +464,7 @@ def main():
         line["max_err_vs_oracle"] = {
             "mixed": float(err.max()), "mixed_pixels_over_1e-5": int(np.sum(err > 1e-5)),
             "fp64_plain": float(np.abs(out64.cpu().numpy().astype(np.float64)[px] - ref).max()),
+            "fp64_links": float(np.abs(out64l.cpu().numpy().astype(np.float64)[px] - ref).max()),
             "fp32_plain": float(np.abs(out32.cpu().numpy().astype(np.float64)[px] - ref).max()),
             "pixels": int(len(px))}
         for name, w in walks.items():

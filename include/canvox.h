@@ -42,6 +42,8 @@ extern "C" {
 #define CANVOX_PREC_CELL32 3  /* the paper's FP32 cell-local walk, p' s + c per step (Sec. 6.2-6.3) */
 #define CANVOX_PREC_WORLD32 4 /* the same walk with the position in FP32 canvas coordinates (Sec. 6.3 comparison) */
 #define CANVOX_PREC_CELL16 5  /* the cell-local walk with binary16 geometry (the half-precision remark of Sec. 6.3) */
+#define CANVOX_PREC_FP64_LINKS 6 /* the mixed path's traversal (neighbour links, persistent queue) with every time,
+                                    side test and sum in FP64: the precision comparator of the mixed path */
 
 /*
  * One view (Sec. 6.1: the eye position is kept in FP64 canvas coordinates so

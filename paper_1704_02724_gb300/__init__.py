@@ -14,6 +14,7 @@ from .canvox import (  # noqa: F401
     PREC_CELL32,
     PREC_WORLD32,
     PREC_CELL16,
+    PREC_FP64_LINKS,
     lib,
     upload_octree,
     render,

@@ -6,7 +6,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libcanvox.so")
-SOURCES = ["runtime.cu", "trace_mixed.cu", "trace_plain.cu", "trace_local32.cu", "noalloc.cu", "probes.cu", "paint.cu"]
+SOURCES = ["runtime.cu", "trace_mixed.cu", "trace_fp64links.cu", "trace_plain.cu", "trace_local32.cu", "noalloc.cu",
+           "probes.cu", "paint.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]

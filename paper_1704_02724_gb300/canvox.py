@@ -28,6 +28,7 @@ PREC_FP32 = 2
 PREC_CELL32 = 3
 PREC_WORLD32 = 4
 PREC_CELL16 = 5
+PREC_FP64_LINKS = 6
 
 # canvox_camera: 136 bytes (eye, right, up, forward: FP64[3]; tan; width, height; offset; background FP32[4])
 CAMERA_BYTES = 136

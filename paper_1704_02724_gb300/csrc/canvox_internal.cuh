@@ -114,6 +114,8 @@ struct PlainParams {
 // Launchers (trace_mixed.cu, trace_plain.cu, runtime.cu).
 cudaError_t launch_mixed(const MixedParams& p, int grid, int block, cudaStream_t s);  // smem from p.smem_records
 cudaError_t mixed_max_blocks_per_sm(int block, int smem_bytes, int* out);
+cudaError_t launch_fp64links(const MixedParams& p, int grid, int block, cudaStream_t s);  // needs p.tree.ropes
+cudaError_t fp64links_max_blocks_per_sm(int block, int* out);
 cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
 cudaError_t launch_local32(const PlainParams& p, int precision, long long n_pixels, cudaStream_t s);
 cudaError_t launch_hash(const Tree& t, unsigned long long* out, cudaStream_t s);

@@ -235,7 +235,7 @@ int setup_views(const canvox_camera* cams, int n, int tile_w, View* out, int64_t
 int resolve_opts(const canvox_render_opts* in, canvox_render_opts* o) {
     if (in) *o = *in;
     else canvox_default_opts(o);
-    if (o->precision < 0 || o->precision > 5) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
+    if (o->precision < 0 || o->precision > 6) return fail(CANVOX_ERR_INVALID_ARG, "precision %d", o->precision);
     if (o->block_threads == 0) o->block_threads = 256;
     if (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32)
         return fail(CANVOX_ERR_INVALID_ARG, "block_threads %d (multiple of 32, at most 256)", o->block_threads);
@@ -287,7 +287,18 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
     CK(cudaMemcpyAsync(g.d_views, hv, sizeof(View) * (size_t)n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(views)");
     CK(cudaMemsetAsync(g.d_scratch, 0, scratch_bytes(queues), s), "cudaMemsetAsync(scratch)");
     const Tree t = device_tree();
-    if (o.precision == CANVOX_PREC_MIXED) {
+    if (o.precision == CANVOX_PREC_MIXED || o.precision == CANVOX_PREC_FP64_LINKS) {
+        // the persistent traversal: mixed precision, or its FP64 twin (same traversal, FP64 arithmetic)
+        const bool f64 = o.precision == CANVOX_PREC_FP64_LINKS;
+        int bps = o.blocks_per_sm;
+        if (f64) {
+            int b = 0;
+            CK(fp64links_max_blocks_per_sm(o.block_threads, &b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+            bps = b > 0 ? (b < bps ? b : bps) : 1;
+        }
+        auto launch = [&](const MixedParams& p, int grid) {
+            return f64 ? launch_fp64links(p, grid, o.block_threads, s) : launch_mixed(p, grid, o.block_threads, s);
+        };
         CK(launch_eye_paths(t, g.d_views, n, g.d_eye, s), "eye path kernel launch");
         MixedParams p;
         std::memset(&p, 0, sizeof(p));
@@ -310,8 +321,8 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
             p.total_rays = total_rays;
             p.ray_base = 0;
             p.queue = g.d_scratch->queue;
-            const int grid = g.sm_count * o.blocks_per_sm;
-            CK(launch_mixed(p, grid, o.block_threads, s), "mixed kernel launch");
+            const int grid = g.sm_count * bps;
+            CK(launch(p, grid), "traversal kernel launch");
         } else {
             for (int v = 0; v < n; ++v) {
                 p.views = g.d_views + v;
@@ -322,9 +333,9 @@ int enqueue(const View* hv, const View* views_host, int n, int64_t total_rays, f
                 p.ray_base = views_host[v].ray_begin;
                 p.queue = g.d_scratch->queue + v;
                 int64_t blocks = (rays + o.block_threads - 1) / o.block_threads;
-                int64_t cap = (int64_t)g.sm_count * o.blocks_per_sm;
+                int64_t cap = (int64_t)g.sm_count * bps;
                 const int grid = (int)(blocks < cap ? blocks : cap);
-                CK(launch_mixed(p, grid > 0 ? grid : 1, o.block_threads, s), "mixed kernel launch");
+                CK(launch(p, grid > 0 ? grid : 1), "traversal kernel launch");
             }
         }
     } else {

@@ -102,6 +102,44 @@ def test_skewed_camera_frames():
         assert max_err(img, img_o) <= tol, prec
 
 
+@pytest.mark.parametrize("seed,depth,extent", [(1, 5, 1.0), (3, 7, 1000.0), (4, 4, 40000.0)])
+def test_fp64_links_twin_random_trees(seed, depth, extent):
+    """The FP64 twin of the mixed traversal (same neighbour links and queue, FP64 arithmetic) against the
+    oracle at 1e-6 on the edge cameras. (Leaf counts are compared on c0 below: these views put rays on cell
+    planes and through edges, where the twin's product form M inv + nod and the oracle's (M - o) / d round
+    differently and may add or drop zero-length segments, which change no pixel.)"""
+    cv = rt.random_tree(depth, seed=500 + seed, p_refine=0.5, extent=extent)
+    cams = _edge_cameras(extent)
+    ref = oracle.render(cv, cams)
+    written = ~np.isnan(ref[:, 0])
+    img, st = render(cv, cams, key=("rt", seed), precision=cx.PREC_FP64_LINKS)
+    assert np.all(np.isnan(img[~written]))
+    assert max_err(img[written], ref[written]) <= 1e-6
+    assert st["rays"] == int(written.sum()) and st["status"] == 0
+
+
+def test_fp64_links_twin_c0_and_deep_scene():
+    """The FP64 twin on the c0 canvas (full image, counters against the oracle's) and on a scene embedded at
+    depth 26 of a 40 km canvas, where canvas-coordinate FP32 fails."""
+    cv = config_canvas(0)
+    cams = synth.config_cameras(0)
+    ref, ic, _ = oracle.render(cv, cams, counters=True)
+    img, st = render(cv, cams, key="c0", precision=cx.PREC_FP64_LINKS)
+    assert max_err(img, ref) <= 1e-6
+    assert abs(st["steps"] - ic[:, 0].sum()) <= 1e-4 * ic[:, 0].sum()
+    assert abs(st["slot_reads"] - ic[:, 1].sum()) <= 1e-4 * ic[:, 1].sum()
+    cv, lo, s = _embedded_scene(26)
+    centre = lo + 0.5 * s
+    cams = synth.cameras_array([
+        synth.look_at_camera(centre + np.array([1.7, 0.6, -1.3]) * s, centre, [0, 1, 0], 0.7, 48, 40, 0,
+                             (0.1, 0.2, 0.3, 1.0)),
+        synth.look_at_camera(centre + np.array([0.1, -0.2, 0.15]) * s, centre + np.array([0.4, 0.3, 0.2]) * s,
+                             [0, 1, 0], 1.0, 32, 32, 48 * 40, (0.1, 0.2, 0.3, 1.0))])
+    ref = oracle.render(cv, cams)
+    img, _ = render(cv, cams, key=("deep", 26), precision=cx.PREC_FP64_LINKS)
+    assert max_err(img, ref) <= 1e-6
+
+
 def test_t_min_zero_runs_to_canvas_exit():
     cv = rt.random_tree(6, seed=77, p_refine=0.55, sigma_range=(0.5, 30.0))
     cams = _edge_cameras(1.0)
