@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 baseline, e2e and CPU baseline")
+    ap.add_argument("--no-deep", action="store_true", help="skip the depth-27 workloads (configs 3 and 4)")
     ap.add_argument("--opts", type=str, default="", help="render options as JSON")
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default schedule")
     ap.add_argument("--res-scale", type=float, default=1.0, help="shrink every image side (profiling cases)")
@@ -247,6 +248,62 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def deep_workloads(cx, synth, torch, stream, flush, dev, topts, steps=5):
+    """The depth-27 canvas of 1,000,000 fine stamps (configs 3 and 4), painted on the GPU from its stamp table;
+    config 3's eight stereo pairs in one persistent launch replayed from a CUDA graph, config 4's 64 uneven views
+    batched (one launch) and one launch per view. Max error against the oracle on seeded pixel samples, the
+    oracle reading the host painter's pools of the same stamps."""
+    import oracle
+    out = {}
+    D, E, c, r, q, _ = synth.config_stamps(3)
+    t = time.perf_counter()
+    nr, nl = cx.paint_spheres(D, E, c, r, q)
+    paint_s = time.perf_counter() - t
+    canvas = None
+    for cid in (3, 4):
+        cams = synth.config_cameras(cid)
+        n_px = synth.total_pixels(cams)
+        img = torch.empty((n_px, 4), dtype=torch.float32, device=dev)
+        runs = {"graph": dict(topts, use_graph=1)} if cid == 3 else \
+            {"batched": dict(topts), "per_view": dict(topts, per_view=1)}
+        res = {}
+        for name, o in runs.items():
+            for _ in range(3):
+                cx.render(cams, img, **o)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cx.render(cams, img, **o)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            res[name] = {"Mrays_s": n_px / (statistics.median(ms) * 1e-3) / 1e6, "ms": statistics.median(ms)}
+        host = img.cpu().numpy().astype(np.float64)   # the last run's image (graph / per-view launches)
+        if canvas is None:
+            t = time.perf_counter()
+            canvas = synth.build_config(3)
+            host_s = time.perf_counter() - t
+        rng = np.random.default_rng(1704 + cid)
+        px = np.sort(rng.choice(n_px, size=min(n_px, 200000), replace=False)).astype(np.int64)
+        ref = oracle.render(canvas, cams, px_idx=px)
+        err = np.abs(host[px] - ref).max(axis=1)
+        key = "c3" if cid == 3 else "c4"
+        out[key] = {"workload": synth.CONFIGS[cid]["name"] + f" ({len(cams)} views, {n_px} rays, depth {D},"
+                                                               f" {nr} records, {nl} leaves)",
+                    "timings": res, "max_err_vs_oracle": float(err.max()), "pixels_over_1e-5": int(np.sum(err > 1e-5)),
+                    "oracle_pixels": int(px.size), "l2": "flushed before every timed render"}
+        if cid == 3:
+            out[key]["stereo_fps"] = 8 / (res["graph"]["ms"] * 1e-3)
+            out[key]["device_painter_seconds"] = round(paint_s, 2)
+            out[key]["host_painter_seconds"] = round(host_s, 1)
+        else:
+            out[key]["batched_over_per_view"] = res["per_view"]["ms"] / res["batched"]["ms"]
+    return out
 
 
 def main():
@@ -501,6 +558,9 @@ def main():
             "identical_to_host_pools": same_full and same_app,
             "append_last_stamps": int(r_.shape[0] - k_), "append_seconds": round(app_s, 3),
             "append_h2d_bytes": int((r_.shape[0] - k_) * 56)}
+        if cid == 2 and not args.no_deep:
+            del canvas
+            line.update(deep_workloads(cx, synth, torch, stream, flush, dev, topts))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

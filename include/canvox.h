@@ -149,16 +149,21 @@ void canvox_default_opts(canvox_render_opts* o);
  *                Slot k of record r is child k = x + 2y + 4z (x, y, z = high
  *                half on that axis; Sec. 4.1.1: eight children per allocation
  *                unit, consecutive indices): v > 0 index of the child's record,
- *                v == 0 empty leaf (extinction 0), v < 0 leaf index -v-1.
+ *                v == 0 empty leaf (extinction 0), v < 0 a stored leaf. Stored
+ *                leaves are numbered 0, 1, ... in breadth-first slot order
+ *                (records in order, slots k = 0..7 within a record), and the
+ *                slot holds -(number mod 2^31) - 1: below 2^31 leaves, -v-1 is
+ *                the number itself; larger pools (up to 2^34 leaves) wrap.
  *   leaf_rgba  : host uint16[n_leaves][4], IEEE FP16 bits (R, G, B, sigma); sigma is
  *                the extinction per canvas unit (finite, >= 0); R, G, B finite.
+ *                Leaf i is row i (n_leaves <= 2^34, n_records <= 2^31 - 1).
  *   depth      : deepest level allowed (1..30); the finest cell is extent * 2^-depth.
  *   extent     : canvas side (> 0, finite, at most 23 significant bits so that
  *                every cell plane is exact in FP64).
  * The upload also builds six neighbour links per record (48 bytes per record) for the
  * default traversal. Validation (CANVOX_ERR_BAD_TREE on failure, previous canvas kept): internal
  * children numbered 1, 2, ... in breadth-first order (each referenced once,
- * no cycles), leaves numbered 0, 1, ... in the same order, no record deeper
+ * no cycles), leaves numbered 0, 1, ... in the same order (modulo 2^31), no record deeper
  * than depth - 1, leaf values finite with sigma >= 0. The host pools may be
  * freed on return. A 64-bit hash of the device copy is checked against the
  * host pools before the call returns.
@@ -183,7 +188,7 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
  * freed first (also on failure). Temporary device memory: per tree level, the ordered
  * stamp lists of the refined cells. n_records, n_leaves (optional) receive the pool
  * sizes. Errors: INVALID_ARG (non-finite input, negative radius or extinction, bad
- * depth/extent), OOM (device memory, or pools beyond int32 indices), CUDA.
+ * depth/extent), OOM (device memory, or pools beyond 2^31 - 1 records or 2^34 leaves), CUDA.
  */
 int canvox_paint_spheres(int32_t depth, double extent, const double* centers, const double* radii,
                          const float* rgba, int64_t n, int64_t* n_records, int64_t* n_leaves);

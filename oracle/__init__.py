@@ -26,17 +26,19 @@ def lib():
     global _lib
     if _lib is None:
         L = ctypes.CDLL(_build.build())
-        L.oracle_render.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+        L.oracle_leaf_base.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.oracle_leaf_base.restype = None
+        L.oracle_render.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                     ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_int32]
         L.oracle_render.restype = ctypes.c_int64
-        L.oracle_trace_rays.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+        L.oracle_trace_rays.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]
         L.oracle_trace_rays.restype = ctypes.c_int64
-        L.oracle_footprint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+        L.oracle_footprint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
         L.oracle_footprint.restype = ctypes.c_int64
@@ -53,12 +55,22 @@ def max_threads():
     return int(lib().oracle_max_threads())
 
 
-def _pools(nodes, leaves):
-    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
-    leaves = np.ascontiguousarray(leaves, dtype=np.uint16)
+def _pools(canvas):
+    """(nodes, leaves, leaf_base): the pools as C arrays and, per record, the number of leaf slots in the
+    records before it (the oracle's leaf numbering; cached on the canvas object when it allows it)."""
+    nodes = np.ascontiguousarray(canvas.nodes, dtype=np.int32)
+    leaves = np.ascontiguousarray(canvas.leaves, dtype=np.uint16)
     if leaves.size == 0:
         leaves = np.zeros((1, 4), dtype=np.uint16)
-    return nodes, leaves
+    base = getattr(canvas, "_oracle_leaf_base", None)
+    if base is None or base.shape[0] != nodes.shape[0]:
+        base = np.empty(max(nodes.shape[0], 1), dtype=np.int64)
+        lib().oracle_leaf_base(nodes.ctypes.data, nodes.shape[0], base.ctypes.data)
+        try:
+            canvas._oracle_leaf_base = base
+        except AttributeError:
+            pass
+    return nodes, leaves, base
 
 
 def render(canvas, cams, px_idx=None, t_min=T_MIN_DEFAULT, threads=0, counters=False, max_steps=0):
@@ -68,7 +80,7 @@ def render(canvas, cams, px_idx=None, t_min=T_MIN_DEFAULT, threads=0, counters=F
     steps, slot reads from the LCA, leaf loads; dcount float64 [n, 2] = sum of
     crossed cell widths, ray length in the canvas).
     """
-    nodes, leaves = _pools(canvas.nodes, canvas.leaves)
+    nodes, leaves, base = _pools(canvas)
     cams = np.ascontiguousarray(cams)
     assert cams.dtype.itemsize == 136
     n_views = cams.shape[0]
@@ -84,7 +96,8 @@ def render(canvas, cams, px_idx=None, t_min=T_MIN_DEFAULT, threads=0, counters=F
     out = np.empty((n, 4), dtype=np.float64)
     ic = np.zeros((n, 3), dtype=np.int64) if counters else None
     dc = np.zeros((n, 2), dtype=np.float64) if counters else None
-    rc = lib().oracle_render(nodes.ctypes.data, leaves.ctypes.data, int(canvas.depth), float(canvas.extent),
+    rc = lib().oracle_render(nodes.ctypes.data, leaves.ctypes.data, base.ctypes.data, int(canvas.depth),
+                             float(canvas.extent),
                              cams.ctypes.data if n_views else None, int(n_views), idx_ptr, int(n),
                              float(t_min), int(max_steps), out.ctypes.data,
                              ic.ctypes.data if counters else None, dc.ctypes.data if counters else None,
@@ -97,7 +110,7 @@ def render(canvas, cams, px_idx=None, t_min=T_MIN_DEFAULT, threads=0, counters=F
 def trace_rays(canvas, origins, directions, background=(0, 0, 0, 0), t_min=T_MIN_DEFAULT, counters=False,
                max_steps=0):
     """Trace explicit rays (directions are normalised in FP64)."""
-    nodes, leaves = _pools(canvas.nodes, canvas.leaves)
+    nodes, leaves, base = _pools(canvas)
     o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
     d = np.ascontiguousarray(directions, dtype=np.float64).reshape(-1, 3)
     bg = np.ascontiguousarray(background, dtype=np.float32)
@@ -105,7 +118,8 @@ def trace_rays(canvas, origins, directions, background=(0, 0, 0, 0), t_min=T_MIN
     out = np.empty((n, 4), dtype=np.float64)
     ic = np.zeros((n, 3), dtype=np.int64)
     dc = np.zeros((n, 2), dtype=np.float64)
-    rc = lib().oracle_trace_rays(nodes.ctypes.data, leaves.ctypes.data, int(canvas.depth), float(canvas.extent),
+    rc = lib().oracle_trace_rays(nodes.ctypes.data, leaves.ctypes.data, base.ctypes.data, int(canvas.depth),
+                                 float(canvas.extent),
                                  o.ctypes.data, d.ctypes.data, n, bg.ctypes.data, float(t_min), int(max_steps),
                                  out.ctypes.data, ic.ctypes.data, dc.ctypes.data)
     if rc != 0:
@@ -118,7 +132,7 @@ def footprint(canvas, cams, t_min=T_MIN_DEFAULT, threads=0):
 
     Returns (rec_mark bool [n_records], leaf_mark bool [n_leaves], rgba [n_pixels, 4]).
     """
-    nodes, leaves = _pools(canvas.nodes, canvas.leaves)
+    nodes, leaves, base = _pools(canvas)
     cams = np.ascontiguousarray(cams)
     n_views = cams.shape[0]
     n = 0
@@ -127,7 +141,8 @@ def footprint(canvas, cams, t_min=T_MIN_DEFAULT, threads=0):
     out = np.empty((max(n, 1), 4), dtype=np.float64)
     rm = np.zeros(max(nodes.shape[0], 1), dtype=np.uint8)
     lm = np.zeros(max(leaves.shape[0], 1), dtype=np.uint8)
-    rc = lib().oracle_footprint(nodes.ctypes.data, leaves.ctypes.data, int(canvas.depth), float(canvas.extent),
+    rc = lib().oracle_footprint(nodes.ctypes.data, leaves.ctypes.data, base.ctypes.data, int(canvas.depth),
+                                float(canvas.extent),
                                 cams.ctypes.data if n_views else None, int(n_views), float(t_min), out.ctypes.data,
                                 rm.ctypes.data, lm.ctypes.data, int(threads))
     if rc != 0:

@@ -27,7 +27,12 @@
  * the same formula, so t increases strictly and each plane is crossed once.
  *
  * Pools (Sec. 4.1.1): record r = 8 int32 slots, child k = x + 2y + 4z;
- * slot > 0 child record, 0 empty leaf, < 0 leaf -slot-1 with FP16 (R,G,B,sigma).
+ * slot > 0 child record, 0 empty leaf, < 0 a stored leaf with FP16 (R,G,B,sigma).
+ * Stored leaves are numbered 0, 1, ... in breadth-first slot order (records in
+ * order, slots k = 0..7 within a record). The oracle takes a leaf's number as
+ * that count itself: the leaf slots of the records before it (leaf_base[r],
+ * from oracle_leaf_base) plus those before it in its record. It does not read
+ * the number the slot stores (the same number, modulo 2^31).
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,9 +53,26 @@ typedef struct {
 typedef struct {
     const int32_t *nodes;
     const uint16_t *leaves;
+    const int64_t *leaf_base;  /* leaf slots in records 0 .. r-1 */
     int32_t depth;
     double extent;
 } otree;
+
+/* leaf_base[r] = number of leaf slots (slot < 0) in records 0 .. r-1. */
+void oracle_leaf_base(const int32_t *nodes, int64_t n_rec, int64_t *leaf_base) {
+    int64_t c = 0;
+    for (int64_t r = 0; r < n_rec; ++r) {
+        leaf_base[r] = c;
+        for (int k = 0; k < 8; ++k) c += nodes[8 * r + k] < 0;
+    }
+}
+
+/* Number of the stored leaf in slot k of record rec: the leaf slots before it in breadth-first slot order. */
+static int64_t leaf_number(const otree *T, int32_t rec, int k) {
+    int64_t li = T->leaf_base[rec];
+    for (int j = 0; j < k; ++j) li += T->nodes[8 * (int64_t)rec + j] < 0;
+    return li;
+}
 
 /* IEEE 754 binary16 -> double (exact): sign, 5-bit exponent (bias 15), 10-bit fraction. */
 static double half_to_double(uint16_t h) {
@@ -173,14 +195,15 @@ static void trace(const otree *T, const double o[3], const double d[3], const fl
             if (te > t1) te = t1;
             double l = te - t;
             if (slot < 0) {
-                const uint16_t *v = T->leaves + 4 * (int64_t)(-slot - 1);
+                const int64_t li = leaf_number(T, rec, path[L - 1]);
+                const uint16_t *v = T->leaves + 4 * li;
                 double sg = half_to_double(v[3]);
                 cnt->leaf_loads += 1;
                 if (leaf_mark) {
 #ifdef _OPENMP
 #pragma omp atomic write
 #endif
-                    leaf_mark[-slot - 1] = 1;
+                    leaf_mark[li] = 1;
                 }
                 if (sg > 0.0) {
                     double a = -expm1(-sg * l);
@@ -204,13 +227,14 @@ static void trace(const otree *T, const double o[3], const double d[3], const fl
  * Returns 0, -1 for bad arguments, or the number of rays that hit the
  * step guard (an oracle bug; those pixels are NaN).
  */
-static int64_t render_pixels(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
-                             const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
+static int64_t render_pixels(const int32_t *nodes, const uint16_t *leaves, const int64_t *leaf_base, int32_t depth,
+                             double extent, const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
                              double t_min, int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount,
                              int32_t n_threads, unsigned char *rec_mark, unsigned char *leaf_mark) {
-    if (!nodes || depth < 1 || depth > 30 || !(extent > 0.0) || n_views < 0 || (n_views && !cams) || !out_rgba)
+    if (!nodes || !leaf_base || depth < 1 || depth > 30 || !(extent > 0.0) || n_views < 0 || (n_views && !cams) ||
+        !out_rgba)
         return -1;
-    otree T = {nodes, leaves, depth, extent};
+    otree T = {nodes, leaves, leaf_base, depth, extent};
     if (max_steps <= 0) max_steps = 3 * ((int64_t)1 << depth) + 8;
     int64_t total = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -250,12 +274,12 @@ static int64_t render_pixels(const int32_t *nodes, const uint16_t *leaves, int32
     return bad;
 }
 
-int64_t oracle_render(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
-                      const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
+int64_t oracle_render(const int32_t *nodes, const uint16_t *leaves, const int64_t *leaf_base, int32_t depth,
+                      double extent, const ocam *cams, int32_t n_views, const int64_t *px_idx, int64_t n_px,
                       double t_min, int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount,
                       int32_t n_threads) {
-    return render_pixels(nodes, leaves, depth, extent, cams, n_views, px_idx, n_px, t_min, max_steps, out_rgba,
-                         icount, dcount, n_threads, NULL, NULL);
+    return render_pixels(nodes, leaves, leaf_base, depth, extent, cams, n_views, px_idx, n_px, t_min, max_steps,
+                         out_rgba, icount, dcount, n_threads, NULL, NULL);
 }
 
 /*
@@ -265,20 +289,20 @@ int64_t oracle_render(const int32_t *nodes, const uint16_t *leaves, int32_t dept
  * leaf_mark[n_leaves] bytes, set to 1. This is the footprint of the traversal
  * (the distinct data a render from a cold cache must read).
  */
-int64_t oracle_footprint(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
-                         const ocam *cams, int32_t n_views, double t_min, double *out_rgba,
+int64_t oracle_footprint(const int32_t *nodes, const uint16_t *leaves, const int64_t *leaf_base, int32_t depth,
+                         double extent, const ocam *cams, int32_t n_views, double t_min, double *out_rgba,
                          unsigned char *rec_mark, unsigned char *leaf_mark, int32_t n_threads) {
     if (!rec_mark || !leaf_mark) return -1;
-    return render_pixels(nodes, leaves, depth, extent, cams, n_views, NULL, 0, t_min, 0, out_rgba, NULL, NULL,
-                         n_threads, rec_mark, leaf_mark);
+    return render_pixels(nodes, leaves, leaf_base, depth, extent, cams, n_views, NULL, 0, t_min, 0, out_rgba, NULL,
+                         NULL, n_threads, rec_mark, leaf_mark);
 }
 
 /* Trace explicit rays (origin, direction not necessarily unit). For tests of single rays. */
-int64_t oracle_trace_rays(const int32_t *nodes, const uint16_t *leaves, int32_t depth, double extent,
-                          const double *orig, const double *dir, int64_t n, const float *bg, double t_min,
-                          int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount) {
-    if (!nodes || depth < 1 || depth > 30 || !(extent > 0.0)) return -1;
-    otree T = {nodes, leaves, depth, extent};
+int64_t oracle_trace_rays(const int32_t *nodes, const uint16_t *leaves, const int64_t *leaf_base, int32_t depth,
+                          double extent, const double *orig, const double *dir, int64_t n, const float *bg,
+                          double t_min, int64_t max_steps, double *out_rgba, int64_t *icount, double *dcount) {
+    if (!nodes || !leaf_base || depth < 1 || depth > 30 || !(extent > 0.0)) return -1;
+    otree T = {nodes, leaves, leaf_base, depth, extent};
     if (max_steps <= 0) max_steps = 3 * ((int64_t)1 << depth) + 8;
     int64_t bad = 0;
     for (int64_t q = 0; q < n; ++q) {

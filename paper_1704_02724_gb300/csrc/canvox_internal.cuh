@@ -14,6 +14,10 @@ namespace canvox {
 // launch is lane g % 32 of tile g / 32.
 constexpr int kMaxDepth = 30;
 constexpr int kMaxSmemRecords = 6144;
+// Leaves are numbered in breadth-first slot order; a slot holds the number modulo 2^31 (-v - 1 for
+// v < 0). The number passes a multiple of 2^31 at most kMaxWraps times: pools of up to 8 x 2^31 leaves.
+constexpr int kMaxWraps = 7;
+constexpr int64_t kMaxLeaves = (int64_t)(kMaxWraps + 1) << 31;
 
 // Device view of the uploaded canvas.
 struct Tree {
@@ -23,10 +27,22 @@ struct Tree {
     int64_t n_rec;
     int64_t n_leaf;
     int32_t depth;
-    int32_t pad;
+    int32_t n_wrap;  // multiples of 2^31 the leaf numbers pass
     double extent;
     double half;  // extent / 2
+    int64_t wrap[kMaxWraps];  // slot position 8 r + k of leaf m 2^31 (m = 1 .. n_wrap), increasing
 };
+
+// Number of the leaf in slot k of record rec, whose value is v < 0: the slot holds its low 31 bits
+// (-v - 1); each wrap position at or before this slot adds 2^31.
+__host__ __device__ __forceinline__ int64_t leaf_index(const Tree& t, int64_t rec, int k, int32_t v) {
+    int64_t li = -((int64_t)v + 1);
+    if (t.n_wrap > 0) {
+        const int64_t pos = rec * 8 + k;
+        for (int m = 0; m < t.n_wrap; ++m) li += pos >= t.wrap[m] ? ((int64_t)1 << 31) : 0;
+    }
+    return li;
+}
 
 // Per-view set-up, computed on the host in FP64 from canvox_camera (host code is
 // compiled without contraction, so the frame is the one the camera model defines).
@@ -125,7 +141,7 @@ cudaError_t probe_l2_gather(int64_t buffer_bytes, double* gbs);
 cudaError_t probe_fp64(double* gflops);
 cudaError_t paint_pools(int32_t depth, double extent, const double* d_centers, const double* d_radii, const float4* d_rgba,
                         int64_t n, int32_t** d_nodes, uint2** d_leaves, int64_t* n_rec, int64_t* n_leaf,
-                        std::vector<int64_t>* level_begin);
+                        std::vector<int64_t>* level_begin, int64_t* wrap, int32_t* n_wrap);  // wrap: kMaxWraps
 cudaError_t scan_i64(int64_t* d, int64_t n, int64_t* total);
 cudaError_t footprint_finish(const int32_t* nodes, const int64_t* level_begin, int n_levels, uint32_t* rec_bits,
                              int64_t rec_words, const uint32_t* leaf_bits, int64_t leaf_words,

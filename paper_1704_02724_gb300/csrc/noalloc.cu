@@ -123,7 +123,7 @@ extern "C" int canvox_render_noalloc(const int32_t* node_pool_dev, int64_t n_rec
     t.n_rec = n_records;
     t.n_leaf = n_leaves;
     t.depth = depth;
-    t.pad = 0;
+    t.n_wrap = 0;  // n_leaves < 2^31: no leaf number passes 2^31
     t.extent = extent;
     t.half = 0.5 * extent;
     if (e == cudaSuccess) e = launch_eye_paths(t, views, n_views, eye, s);

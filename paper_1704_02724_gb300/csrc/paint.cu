@@ -640,9 +640,12 @@ __global__ void survive_count(int64_t n, const uint64_t* slot, const uint64_t* c
 }
 
 // Pool rows of the surviving records of one level.
+// Leaf numbers (breadth-first slot order) are written modulo 2^31; the slot position 8 r + k of each leaf
+// whose number is a nonzero multiple m 2^31 goes to wraps[m - 1].
 __global__ void write_level(int64_t n, const uint64_t* slot, const uint64_t* ckey_next, const int64_t* rec_scan,
                             const int64_t* leaf_scan, const int64_t* surv, int64_t rec_base, int64_t next_rec_base,
-                            int64_t leaf_base, const int64_t* next_rec_scan, int32_t* nodes, uint2* leaves) {
+                            int64_t leaf_base, const int64_t* next_rec_scan, int32_t* nodes, uint2* leaves,
+                            int64_t* wraps) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !surv[i]) return;
     const int64_t r = rec_base + rec_scan[i];
@@ -659,7 +662,9 @@ __global__ void write_level(int64_t n, const uint64_t* slot, const uint64_t* cke
                 out = 0;
             } else {
                 leaves[lf] = make_uint2((uint32_t)key, (uint32_t)(key >> 32));
-                out = -(int32_t)lf - 1;
+                const int64_t low = lf & 0x7FFFFFFFll;
+                out = -(int32_t)low - 1;
+                if (low == 0 && lf > 0) wraps[(lf >> 31) - 1] = 8 * r + k;
                 ++lf;
             }
         }
@@ -755,7 +760,7 @@ unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const double* d_r, const float4* d_rgba,
                         int64_t n, int32_t** d_nodes_out, uint2** d_leaves_out, int64_t* n_rec_out, int64_t* n_leaf_out,
-                        std::vector<int64_t>* level_begin) {
+                        std::vector<int64_t>* level_begin, int64_t* wrap_out, int32_t* n_wrap_out) {
     const double half = 0.5 * extent;
     DevBuf buf;
     // squared radii and target depths (the host painter's integer loop, in the same FP64 operations)
@@ -885,6 +890,10 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const d
         leaf_base[(size_t)l + 1] = leaf_base[(size_t)l] + nlf;
     }
     const int64_t n_rec = rec_base[(size_t)nl], n_leaf = leaf_base[(size_t)nl];
+    if (n_rec > 0x7FFFFFFFll || n_leaf > kMaxLeaves) return cudaErrorMemoryAllocation;  // beyond the pool format
+    const int32_t n_wrap = n_leaf > 0 ? (int32_t)((n_leaf - 1) >> 31) : 0;
+    int64_t* d_wraps;
+    PCK(buf.alloc(&d_wraps, kMaxWraps));
     int32_t* d_nodes = nullptr;
     uint2* d_leaves = nullptr;
     PCK(cudaMalloc(&d_nodes, sizeof(int32_t) * 8 * (size_t)n_rec));
@@ -900,15 +909,19 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const d
         write_level<<<blocks_for(nc, 256), 256>>>(nc, slots[(size_t)l], ckey[(size_t)l + 1], rec_scan[(size_t)l],
                                                    leaf_scan[(size_t)l], surv[(size_t)l], rec_base[(size_t)l],
                                                    rec_base[(size_t)l + 1], leaf_base[(size_t)l],
-                                                   l + 1 < nl ? rec_scan[(size_t)l + 1] : zero_scan, d_nodes, d_leaves);
+                                                   l + 1 < nl ? rec_scan[(size_t)l + 1] : zero_scan, d_nodes, d_leaves,
+                                                   d_wraps);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && n_wrap > 0)
+        e = cudaMemcpy(wrap_out, d_wraps, sizeof(int64_t) * (size_t)n_wrap, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         cudaFree(d_nodes);
         cudaFree(d_leaves);
         return e;
     }
+    *n_wrap_out = n_wrap;
     *d_nodes_out = d_nodes;
     *d_leaves_out = d_leaves;
     *n_rec_out = n_rec;

@@ -64,6 +64,8 @@ struct Ctx {
     int64_t n_rec = 0, n_leaf = 0;
     int32_t depth = 0;
     double extent = 0.0;
+    int32_t n_wrap = 0;             // leaf numbers pass a multiple of 2^31 this many times ...
+    int64_t wrap[kMaxWraps] = {};   // ... at these slot positions 8 r + k
     unsigned long long host_hash = 0;
     std::vector<int64_t> level_begin;  // records of level l: [level_begin[l], level_begin[l + 1])
     bool uploaded = false;
@@ -274,7 +276,8 @@ Tree device_tree() {
     t.n_rec = g.n_rec;
     t.n_leaf = g.n_leaf;
     t.depth = g.depth;
-    t.pad = 0;
+    t.n_wrap = g.n_wrap;
+    for (int m = 0; m < kMaxWraps; ++m) t.wrap[m] = g.wrap[m];
     t.extent = g.extent;
     t.half = 0.5 * g.extent;
     return t;
@@ -447,11 +450,15 @@ int paint_table(int32_t depth, double extent, int64_t* n_records, int64_t* n_lea
     uint2* leaves = nullptr;
     int64_t nr = 0, nl = 0;
     std::vector<int64_t> lb;
-    CK(paint_pools(depth, extent, g.d_st_c, g.d_st_r, g.d_st_rgba, g.st_n, &nodes, &leaves, &nr, &nl, &lb),
-       "device painter");
+    int64_t wraps[kMaxWraps] = {};
+    int32_t n_wrap = 0;
+    CK(paint_pools(depth, extent, g.d_st_c, g.d_st_r, g.d_st_rgba, g.st_n, &nodes, &leaves, &nr, &nl, &lb, wraps,
+                   &n_wrap),
+       "device painter (or a canvas beyond 2^31 - 1 records / 2^34 leaves)");
     g.d_nodes = nodes;
     g.d_leaves = leaves;
-    if (nr > 0x7FFFFFFFll || nl > 0x7FFFFFFFll) return fail(CANVOX_ERR_OOM, "painted canvas exceeds int32 pool indices");
+    g.n_wrap = n_wrap;
+    for (int m = 0; m < kMaxWraps; ++m) g.wrap[m] = m < n_wrap ? wraps[m] : 0;
     g.n_rec = nr;
     g.n_leaf = nl;
     g.depth = depth;
@@ -496,14 +503,16 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     g_err.clear();
     if (!node_pool || n_records < 1 || n_leaves < 0 || (n_leaves > 0 && !leaf_rgba))
         return fail(CANVOX_ERR_INVALID_ARG, "null pool or bad count");
-    if (n_records > 0x7FFFFFFFll || n_leaves > 0x7FFFFFFFll)
-        return fail(CANVOX_ERR_INVALID_ARG, "pool larger than int32 indices");
+    if (n_records > 0x7FFFFFFFll || n_leaves > kMaxLeaves)
+        return fail(CANVOX_ERR_INVALID_ARG, "pool beyond 2^31 - 1 records or 2^34 leaves");
     int rc = check_canvas_args(depth, extent);
     if (rc) return rc;
     // validation: breadth-first numbering of records and leaves, depth bound, finite FP16 values
     std::vector<uint8_t> level((size_t)n_records, 0);
     int64_t next_rec = 1, next_leaf = 0;
     unsigned long long hh = 0;
+    int64_t wraps[kMaxWraps] = {};
+    int32_t n_wrap = 0;
     for (int64_t r = 0; r < n_records; ++r) {
         if (r >= next_rec) return fail(CANVOX_ERR_BAD_TREE, "record %lld is not referenced before it appears", (long long)r);
         for (int k = 0; k < 8; ++k) {
@@ -519,11 +528,16 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
                 level[v] = (uint8_t)(level[r] + 1);
                 ++next_rec;
             } else if (v < 0) {
+                // leaves are numbered in breadth-first slot order; the slot holds the number modulo 2^31
                 const int64_t li = -(int64_t)v - 1;
-                if (li != next_leaf)
-                    return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: leaf %lld, expected %lld (breadth-first order)",
-                                (long long)r, k, (long long)li, (long long)next_leaf);
-                if (li >= n_leaves) return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: leaf %lld out of range", (long long)r, k, (long long)li);
+                if (li != (next_leaf & 0x7FFFFFFFll))
+                    return fail(CANVOX_ERR_BAD_TREE,
+                                "record %lld slot %d: leaf %lld, expected %lld (breadth-first order, modulo 2^31)",
+                                (long long)r, k, (long long)li, (long long)(next_leaf & 0x7FFFFFFFll));
+                if (next_leaf >= n_leaves)
+                    return fail(CANVOX_ERR_BAD_TREE, "record %lld slot %d: leaf %lld out of range", (long long)r, k,
+                                (long long)next_leaf);
+                if (next_leaf > 0 && li == 0) wraps[n_wrap++] = 8 * r + k;  // n_leaves <= 2^34: at most 7
                 ++next_leaf;
             }
         }
@@ -552,6 +566,8 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     g.n_leaf = n_leaves;
     g.depth = depth;
     g.extent = extent;
+    g.n_wrap = n_wrap;
+    for (int m = 0; m < kMaxWraps; ++m) g.wrap[m] = m < n_wrap ? wraps[m] : 0;
     g.host_hash = hh;
     // bit-identity of the device copy
     CK(cudaMemset(g.d_hash, 0, sizeof(unsigned long long)), "cudaMemset(hash)");

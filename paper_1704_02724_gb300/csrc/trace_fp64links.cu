@@ -185,7 +185,7 @@ __device__ bool init64(Ray64& r, const MixedParams& P, unsigned long long g) {
     r.L = lev + 1;
     r.n_reads += r.L;
     if (slot < 0) {
-        r.val = __ldg(T.leaves + (-(int64_t)slot - 1));
+        r.val = __ldg(T.leaves + leaf_index(T, rec, (int)r.kc, slot));
         r.n_leaf += 1;
     } else {
         r.val = make_uint2(0u, 0u);
@@ -264,7 +264,7 @@ __device__ bool step64(Ray64& r, const MixedParams& P) {
     r.n_reads += (uint32_t)(Ln - lstar);
     uint2 nval = make_uint2(0u, 0u);
     if (slot < 0) {
-        nval = __ldg(T.leaves + (-(int64_t)slot - 1));
+        nval = __ldg(T.leaves + leaf_index(T, prec, kk, slot));
         r.n_leaf += 1;
     }
     // 4. composite the current leaf, then terminate or advance

@@ -111,6 +111,8 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
         unsigned c[3] = {0u, 0u, 0u};
         int L = 0;
         int32_t rec = 0, slot;
+        int32_t srec = 0;  // record and child index of the current leaf's slot
+        int sk = 0;
         for (;;) {
             const double w = T.extent * p2d(-(L + 1));
             int k = 0;
@@ -126,6 +128,8 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             slot = __ldg(T.nodes + (long long)rec * 8 + k);
             rec_loads += 1;
             ++L;
+            srec = rec;
+            sk = k;
             if (slot <= 0) break;
             rec = slot;
         }
@@ -167,7 +171,7 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             if (ax < 0) break;
             const float ell = kCellLocal ? __fmul_rn(fmaxf(tef, 0.0f), w) : fmaxf(tef, 0.0f);
             if (slot < 0) {
-                const uint2 q = __ldg(T.leaves + (-(long long)slot - 1));
+                const uint2 q = __ldg(T.leaves + leaf_index(T, srec, sk, slot));
                 leaf_loads += 1;
                 const float s = h2f32((unsigned short)(q.y >> 16));
                 if (s > 0.0f) {
@@ -194,6 +198,8 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
             int Ln, kk;
             int32_t pr;
             slot = locate_int(T, cc, L, &Ln, &pr, &kk, &rec_loads);
+            srec = pr;
+            sk = kk;
             // position in the frame of the same-level neighbour (its centre is one cell further on ax)
             GT q[3];
             for (int a = 0; a < 3; ++a) q[a] = pe[a];
@@ -221,6 +227,8 @@ __device__ Local32Count local32_ray(const PlainParams& P, long long idx) {
                 ++Lc;
                 slot = __ldg(T.nodes + (long long)rec * 8 + k);
                 rec_loads += 1;
+                srec = rec;
+                sk = k;
                 Ln = Lc;
             }
             if (kCellLocal && Ln < L) {

@@ -90,7 +90,10 @@ __device__ __forceinline__ int32_t load_slot(const Tree& T, int32_t n_smem, int3
     if (kSmem && rec < n_smem) return s_nodes[rec * 8 + k];
     return __ldg(T.nodes + (int64_t)rec * 8 + k);
 }
-__device__ __forceinline__ uint2 load_leaf(const Tree& T, int32_t slot) { return __ldg(T.leaves + (-(int64_t)slot - 1)); }
+// Value of the leaf in slot k of record rec (slot value v < 0).
+__device__ __forceinline__ uint2 load_leaf(const Tree& T, int32_t rec, int k, int32_t v) {
+    return __ldg(T.leaves + leaf_index(T, rec, k, v));
+}
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     const float y = __fsub_rn(x, c);
@@ -413,7 +416,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     r.L = lev + 1;
     if (kCount) r.n_reads += r.L;
     if (slot < 0) {
-        r.val = load_leaf(T, slot);
+        r.val = load_leaf(T, rec, (int)r.kc, slot);
         if (kCount) r.n_leaf += 1;
     } else {
         r.val = make_uint2(0u, 0u);
@@ -565,7 +568,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     if (kCount) r.n_reads += (uint32_t)(Ln - lstar);
     uint2 nval = make_uint2(0u, 0u);
     if (slot < 0) {
-        nval = load_leaf(T, slot);
+        nval = load_leaf(T, prec, kk, slot);
         if (kCount) r.n_leaf += 1;
     }
     const bool rebase = fexit || (Ln - r.f > P.frame_levels);

@@ -100,9 +100,10 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
             unsigned cc[3] = {0u, 0u, 0u};
             int lev = 0;
             int32_t rec = 0, slot;
+            int k = 0;
             for (;;) {
                 const R w = E * N::pow2(-(lev + 1));
-                int k = 0;
+                k = 0;
                 for (int a = 0; a < 3; ++a) {
                     const R M = N::fma_((R)(2u * cc[a] + 1u), w, -half);
                     unsigned b;
@@ -137,9 +138,10 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
             te = fmin(te, t1);
             steps += 1;
             if (slot < 0) {
-                const uint2 q = __ldg(T.leaves + (-(long long)slot - 1));
+                const int64_t li = leaf_index(T, rec, k, slot);
+                const uint2 q = __ldg(T.leaves + li);
                 leaf_loads += 1;
-                if (P.mark_leaf) mark_bit(P.mark_leaf, -(long long)slot - 1);
+                if (P.mark_leaf) mark_bit(P.mark_leaf, li);
                 const R s = (R)h2f((unsigned short)(q.y >> 16));
                 if (s > (R)0) {
                     const R l = te - t;
@@ -226,7 +228,7 @@ __global__ void eye_path_kernel(Tree t, const View* views, int n_views, EyePath*
             continue;
         }
         if (slot < 0) {
-            E.val = t.leaves[-(long long)slot - 1];
+            E.val = t.leaves[leaf_index(t, rec, k, slot)];
             E.stored = 1;
         }
         E.c[0] = c[0];

@@ -124,12 +124,12 @@ def stamp_canvas(depth, extent, centers, radii, rgba, root_levels=1):
         if n:
             rc = L.synth_tree_stamp_spheres(h, n, centers.ctypes.data, radii.ctypes.data, rgba.ctypes.data)
             if rc != 0:
-                raise MemoryError("canvas exceeds int32 pool indices")
+                raise MemoryError("more than 2^31 - 1 stamps")
         nb, nv = ctypes.c_int64(), ctypes.c_int64()
         L.synth_tree_sizes(h, ctypes.byref(nb), ctypes.byref(nv))
         nr, nl, ml = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         if L.synth_tree_finalize(h, ctypes.byref(nr), ctypes.byref(nl), ctypes.byref(ml)) != 0:
-            raise MemoryError("leaf pool exceeds int32 indices")
+            raise MemoryError("pools beyond 2^31 - 1 records or 2^34 leaves")
         nodes = np.empty((nr.value, 8), dtype=np.int32)
         leaves = np.empty((nl.value, 4), dtype=np.uint16)
         L.synth_tree_export(h, nodes.ctypes.data, leaves.ctypes.data)

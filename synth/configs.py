@@ -14,10 +14,10 @@ for config 0, metres for configs 1-4. Extinction sigma is per canvas unit.
       (c1 extinction recipe, kept 10 m clear of the rooms) plus 200,000 fine spheres r log-U[2.4 mm, 10 cm]
       in four 1 m room boxes, extinction from an optical thickness 2 r sigma log-U[0.002, 0.2];
       stereo pair 2160x2160 per eye, 90 deg, eye separation 64 mm, head inside room 0.
-  c3  depth 27, 40 km canvas (finest 0.3 mm): recipe of c2 with fine spheres r log-U[0.3 mm, 10 cm];
-      8 stereo pairs (4 rooms x scales 1 and 0.01). 100,000 fine spheres by default: with ten cells
-      per brush radius each fine sphere adds about 3,300 leaves at depth 27, so the 1,000,000 of the
-      workload description would need about 3.3e9 leaves, beyond 32-bit leaf indices.
+  c3  depth 27, 40 km canvas (finest 0.3 mm): recipe of c2 with 1,000,000 fine spheres r log-U[0.3 mm, 10 cm];
+      8 stereo pairs (4 rooms x scales 1 and 0.01). With ten cells per brush radius each fine sphere adds
+      about 3,000 leaves at depth 27: about 3.1e9 leaves and 4.6e8 records, so leaf numbers pass 2^31
+      (the pool format stores them modulo 2^31).
   c4  the c3 canvas; 64 views, square side log-U[256, 2160], camera scale log-U[1 mm, 10 km].
 """
 import math
@@ -32,8 +32,8 @@ CONFIGS = {
     0: dict(name="c0_depth8_unit_cube_256sq", depth=8, extent=1.0),
     1: dict(name="c1_depth16_1km_1080p", depth=16, extent=1000.0),
     2: dict(name="c2_depth24_40km_stereo2160", depth=24, extent=40000.0),
-    3: dict(name="c3_depth27_40km_8stereo2160", depth=27, extent=40000.0),
-    4: dict(name="c4_depth27_40km_64views", depth=27, extent=40000.0),
+    3: dict(name="c3_depth27_40km_1M_fine_stamps_8stereo2160", depth=27, extent=40000.0),
+    4: dict(name="c4_depth27_40km_1M_fine_stamps_64views", depth=27, extent=40000.0),
 }
 
 ROOM_SIZE = 1.0
@@ -123,7 +123,7 @@ def config_stamps(cid, n_fine=None):
         c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 200_000, E / 2.0 ** D)
     elif cid in (3, 4):
         rng = Rng(SEED_BASE + 3)
-        c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 100_000, E / 2.0 ** D)
+        c, r, q, rooms = _deep_stamps(rng, E, D, 10_000, n_fine or 1_000_000, E / 2.0 ** D)
     else:
         raise KeyError(cid)
     return D, E, np.ascontiguousarray(c, dtype=np.float64), np.ascontiguousarray(r, dtype=np.float64), \

@@ -19,7 +19,9 @@
 // (Sec. 4.1.1: in its quadtree example the cell above the first child is at offset 2, so +2 is y):
 //   slot > 0  : index of the child's record (always > r, breadth-first order)
 //   slot == 0 : empty leaf (extinction 0)
-//   slot < 0  : leaf index -slot-1 into the leaf pool of 4 x FP16 (R,G,B,sigma)
+//   slot < 0  : a stored leaf of the leaf pool of 4 x FP16 (R,G,B,sigma). Leaves are numbered
+//               0, 1, ... in breadth-first slot order, and the slot holds -(number mod 2^31) - 1,
+//               so pools can pass 2^31 leaves with 32-bit slots (below 2^31, -slot-1 is the number).
 // Record 0 is the root cell [-E/2, E/2]^3.
 #include <cstdint>
 #include <cstring>
@@ -334,8 +336,8 @@ int bfs(Builder& B, int32_t* nodes, uint16_t* leaves, int64_t* n_rec, int64_t* n
             } else if (s.key == 0) {
                 out = 0;
             } else {
-                if (nl >= 0x7FFFFFFF) return -1;
-                out = -(int32_t)nl - 1;
+                if (nl >= ((int64_t)8 << 31)) return -1;  // beyond 2^34 leaves
+                out = -(int32_t)(nl & 0x7FFFFFFF) - 1;
                 if (leaves)
                     for (int c = 0; c < 4; ++c) leaves[4 * nl + c] = (uint16_t)(s.key >> (16 * c));
                 ++nl;

@@ -15,7 +15,7 @@ def config_canvas(cid, n_fine=None):
     return _config_canvas(3 if cid == 4 else cid, n_fine)   # c4 renders the c3 canvas
 
 
-@functools.lru_cache(maxsize=3)
+@functools.lru_cache(maxsize=4)
 def _config_canvas(cid, n_fine):
     return synth.build_config(cid, n_fine=n_fine)
 

@@ -332,3 +332,28 @@ def test_walk32_within_the_paper_bound():
     assert np.max(an) <= math.degrees(math.asin(math.sqrt(2) * (e0 / 1.5 + 7.5 * eps)))
     st_w, an_w = oracle.walk32(cv, cams, cell_local=False)
     assert np.max(an_w) > np.max(an)
+
+
+def test_leaf_numbers_are_the_breadth_first_slot_rank():
+    """Stored leaves are numbered 0, 1, ... in breadth-first slot order (Sec. 4.1.1's index pools), and the slot
+    holds the number modulo 2^31. The generator's pools: -slot-1 is that rank for every leaf slot (canvases
+    below 2^31 leaves). The oracle's per-record base equals a numpy prefix count, and the oracle reads leaves
+    by the rank alone: pools whose leaf slots all hold -1 render identically."""
+    cv = synth.stamp_canvas(6, 1.0, *[a for a in _stamps(7)])
+    neg = cv.nodes < 0
+    rank = np.cumsum(neg.ravel()) - 1
+    np.testing.assert_array_equal((-cv.nodes.ravel()[neg.ravel()] - 1), rank[neg.ravel()])
+    base = np.empty(cv.n_records, dtype=np.int64)
+    oracle.lib().oracle_leaf_base(np.ascontiguousarray(cv.nodes).ctypes.data, cv.n_records, base.ctypes.data)
+    np.testing.assert_array_equal(base, np.concatenate([[0], np.cumsum(neg.sum(axis=1))[:-1]]))
+    blind = synth.Canvas(nodes=np.where(neg, -1, cv.nodes).astype(np.int32), leaves=cv.leaves, depth=cv.depth,
+                         extent=cv.extent)
+    o, d = _random_rays(31, 300, 1.0)
+    np.testing.assert_array_equal(oracle.trace_rays(cv, o, d, (0.2, 0.3, 0.4, 1)),
+                                  oracle.trace_rays(blind, o, d, (0.2, 0.3, 0.4, 1)))
+
+
+def _stamps(seed, n=60):
+    rng = synth.Rng(seed)
+    U = rng.uniform(n * 8).reshape(n, 8)
+    return -0.5 + U[:, 0:3], (1.0 + 6.0 * U[:, 3]) / 64.0, np.c_[U[:, 4:7], 0.5 + 19.5 * U[:, 7]].astype(np.float32)

@@ -7,7 +7,7 @@ import pytest
 
 import paper_1704_02724_gb300 as cx
 import synth
-from gpu_util import _uploaded, render
+from gpu_util import _uploaded, config_canvas, render
 
 pytestmark = pytest.mark.gpu
 
@@ -109,3 +109,25 @@ def test_paint_ties_on_cell_planes():
     rng = np.random.default_rng(11)
     q = np.c_[rng.uniform(0, 1, (len(r), 3)), rng.uniform(0.5, 9.0, len(r))].astype(np.float32)
     _paint_and_compare(D, E, c, r, q)
+
+
+def test_paint_depth27_million_stamps_identical_to_host():
+    """The depth-27 canvas of 1,000,000 fine stamps (config 3): more than 2^31 leaves, so the pools store leaf
+    numbers modulo 2^31. The device painter's pools equal the host painter's byte for byte, and the library's
+    own hash of the painted pools equals the host-side hash of the host painter's pools."""
+    ref = config_canvas(3)
+    assert ref.n_leaves > 2 ** 31
+    D, E, c, r, q, _ = synth.config_stamps(3)
+    _uploaded["key"] = None
+    nr, nl = cx.paint_spheres(D, E, c, r, q)
+    assert (nr, nl) == (ref.n_records, ref.n_leaves)
+    _, dev_hash = cx.octree_hash()
+    nodes, leaves = cx.download_octree()
+    assert np.array_equal(nodes, ref.nodes)
+    del nodes
+    assert np.array_equal(leaves, ref.leaves)
+    del leaves
+    cx.upload_octree(ref.nodes, ref.leaves, ref.depth, ref.extent)   # validation passes, hashes agree
+    h, d = cx.octree_hash()
+    assert h == d == dev_hash
+    _uploaded["key"] = None
