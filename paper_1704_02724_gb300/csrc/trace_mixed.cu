@@ -272,11 +272,12 @@ __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
 // is within 2^-23 |F| + 2^-47 (|ih| + |nh|) of the exact time, and the
 // difference D = fl(fl(F - th) - tl) within 2^-23 (|F| + |th| + |D|) more.
 // When |D| exceeds 2^-21 (|F| + |th|) + 2^-42 (|ih| + |nh|) + margin_t (with
-// room for its own rounding) the side is the sign of D; otherwise, and for
-// frames deeper than 22 levels, the side is decided in FP64 at need64().
-template <typename Need64>
-__device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a, uint32_t cc, int lev, float th,
-                                              float tl, float margin_t, Need64 need64) {
+// room for its own rounding) the side is the sign of D. Otherwise, and for
+// frames deeper than 22 levels, it returns kUndecided: the caller decides in
+// FP64 (side64), once per level for all the sides left open.
+constexpr uint32_t kUndecided = 2u;
+__device__ __forceinline__ uint32_t child_side(const Ray& r, int a, uint32_t cc, int lev, float th, float tl,
+                                               float margin_t) {
     if (lev - r.f < kMaxFrameBits) {
         const uint32_t rel = cc & ((1u << (lev - r.f)) - 1u);
         const float Mp = small_uint_to_float(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
@@ -291,9 +292,13 @@ __device__ __forceinline__ uint32_t child_bit(const Ray& r, const Tree& T, int a
             if (fabsf(D) * kOneMinus20 > screen) return r.ih[a] > 0.0f ? (D <= 0.0f) : (D > 0.0f);
         }
     }
-    const double t64 = need64();
+    return kUndecided;
+}
+
+// FP64 side of the mid-plane of cell cc (level lev) on axis a just after FP64 time t.
+__device__ __forceinline__ uint32_t side64(const Ray& r, const Tree& T, int a, uint32_t cc, int lev, double t) {
     const double M = fma((double)(2u * cc + 1u), T.extent * pow2d(-(lev + 1)), -T.half);
-    return high64(r, a, M, t64);
+    return high64(r, a, M, t);
 }
 
 // Start ray g of the launch. Returns true if it has a leaf to step from.
@@ -386,7 +391,6 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     int32_t rec = 0;
     int32_t slot;
     stk[0] = 0;
-    auto need64 = [&]() { return t0; };
     for (;;) {
         if (lev - r.f >= kMaxFrameBits) {
             // planes of the next level need more than 22 bits in this frame: re-anchor at this cell
@@ -394,12 +398,19 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
             r.f = lev;
             set_frame(r, T, inv_extent, t0);
         }
+        uint32_t b3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) b3[a] = child_side(r, a, r.c[a], lev, 0.0f, 0.0f, 0.0f);
+        if (b3[0] == kUndecided || b3[1] == kUndecided || b3[2] == kUndecided) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (b3[a] == kUndecided) b3[a] = side64(r, T, a, r.c[a], lev, t0);
+        }
         int k = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const uint32_t b = child_bit(r, T, a, r.c[a], lev, 0.0f, 0.0f, 0.0f, need64);
-            r.c[a] = 2u * r.c[a] + b;
-            k |= (int)b << a;
+            r.c[a] = 2u * r.c[a] + b3[a];
+            k |= (int)b3[a] << a;
         }
         slot = load_slot<kSmem>(T, P.smem_records, rec, k);
         if (kCount) r.n_rec += 1;
@@ -489,90 +500,85 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         }
         return te64;
     };
-    if ((cn >> r.L) != 0u) {
-        // leaving the canvas: last segment, bounded like a boundary to sigma = 0
-        if (!have64 && (r.val.y >> 16)) {
-            const float need = r.T * hsig(r.val) * r.sf_eps * fabsf(inv_ax);
-            if (ERR(r) + need > P.err_budget) need64();
-            else ERR(r) += need;
-        }
-        composite(r, teh, tel);
-        finish(r, P);
-        return false;
-    }
-    const int lstar = r.L - (32 - __clz(cold ^ cn));
-    const bool fexit = lstar < r.f;
-    if (fexit) need64();
-    // 3. the new leaf: start at the neighbouring cell (a sibling, the parent's neighbour link,
-    //    or the common ancestor on the stack), then descend while the cell is internal
+    const bool leaves_canvas = (cn >> r.L) != 0u;
     uint32_t cc[3] = {ax == 0 ? cn : r.c[0], ax == 1 ? cn : r.c[1], ax == 2 ? cn : r.c[2]};
-    int Lc = r.L;
-    int lv;         // level of the cell in slot (prec, kk)
-    int32_t prec;
-    int kk;
-    if (kRopes) {
-        if (lstar == r.L - 1) {
-            prec = r.pr;
-            kk = (int)(r.kc ^ (1u << ax));
-            lv = r.L;
-        } else {
-            const uint2 rp = __ldg(T.ropes + (int64_t)r.pr * 6 + 2 * ax + (int)up);
-            if (kCount) r.n_rec += 1;
-            prec = (int32_t)rp.x;
-            kk = (int)((rp.y >> 8) & 7u);
-            lv = (int)(rp.y & 255u);
-        }
-    } else {
-        prec = stk[lstar];
-        lv = lstar + 1;
-        const int sh = Lc - lv;
-        kk = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
-    }
-    int32_t slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
-    if (kCount) r.n_rec += 1;
-    const float margin_ax = kEpsDF * fabsf(inv_ax);
-    while (slot > 0) {
-        // internal cell at level lv (record `slot`): choose its child at level lv + 1
-        if (!kRopes) stk[lv] = slot;
-        int k;
-        if (lv < Lc) {
-            const int sh = Lc - 1 - lv;
-            k = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
-        } else {
-            // finer than the old cell: near side on the exit axis, ray position on the others
-            k = 0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                uint32_t bit;
-                if (a == ax) {
-                    bit = up ? 0u : 1u;
-                } else if (fexit) {
-                    const double M = fma((double)(2u * cc[a] + 1u), T.extent * pow2d(-(lv + 1)), -T.half);
-                    bit = high64(r, a, M, te64);
-                } else {
-                    bit = child_bit(r, T, a, cc[a], lv, teh, tel, margin_ax, need64);
-                }
-                cc[a] = 2u * cc[a] + bit;
-                k |= (int)bit << a;
+    int Lc = r.L, Ln = r.L;
+    int32_t prec = 0;
+    int kk = 0;
+    uint2 nval = make_uint2(0u, 0u);  // the next leaf's value (empty past the canvas)
+    bool rebase = false;
+    if (!leaves_canvas) {
+        const int lstar = r.L - (32 - __clz(cold ^ cn));
+        const bool fexit = lstar < r.f;
+        if (fexit) need64();
+        // 3. the new leaf: start at the neighbouring cell (a sibling, the parent's neighbour link,
+        //    or the common ancestor on the stack), then descend while the cell is internal
+        int lv;  // level of the cell in slot (prec, kk)
+        if (kRopes) {
+            if (lstar == r.L - 1) {
+                prec = r.pr;
+                kk = (int)(r.kc ^ (1u << ax));
+                lv = r.L;
+            } else {
+                const uint2 rp = __ldg(T.ropes + (int64_t)r.pr * 6 + 2 * ax + (int)up);
+                if (kCount) r.n_rec += 1;
+                prec = (int32_t)rp.x;
+                kk = (int)((rp.y >> 8) & 7u);
+                lv = (int)(rp.y & 255u);
             }
-            ++Lc;
+        } else {
+            prec = stk[lstar];
+            lv = lstar + 1;
+            const int sh = Lc - lv;
+            kk = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
         }
-        prec = slot;
-        kk = k;
-        ++lv;
-        slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
+        int32_t slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
         if (kCount) r.n_rec += 1;
+        const float margin_ax = kEpsDF * fabsf(inv_ax);
+        while (slot > 0) {
+            // internal cell at level lv (record `slot`): choose its child at level lv + 1
+            if (!kRopes) stk[lv] = slot;
+            int k;
+            if (lv < Lc) {
+                const int sh = Lc - 1 - lv;
+                k = (int)((cc[0] >> sh) & 1u) | (int)(((cc[1] >> sh) & 1u) << 1) | (int)(((cc[2] >> sh) & 1u) << 2);
+            } else {
+                // finer than the old cell: near side on the exit axis, ray position on the others (FP32
+                // screen; FP64 at the exit time for the sides it leaves open, and past a frame exit)
+                uint32_t b3[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    b3[a] = a == ax ? (up ? 0u : 1u)
+                                    : (fexit ? kUndecided : child_side(r, a, cc[a], lv, teh, tel, margin_ax));
+                if (b3[0] == kUndecided || b3[1] == kUndecided || b3[2] == kUndecided) {
+                    const double t64 = need64();
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        if (b3[a] == kUndecided) b3[a] = side64(r, T, a, cc[a], lv, t64);
+                }
+                k = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cc[a] = 2u * cc[a] + b3[a];
+                    k |= (int)b3[a] << a;
+                }
+                ++Lc;
+            }
+            prec = slot;
+            kk = k;
+            ++lv;
+            slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
+            if (kCount) r.n_rec += 1;
+        }
+        Ln = lv;
+        if (kCount) r.n_reads += (uint32_t)(Ln - lstar);
+        if (slot < 0) {
+            nval = load_leaf(T, prec, kk, slot);
+            if (kCount) r.n_leaf += 1;
+        }
+        rebase = fexit || (Ln - r.f > P.frame_levels);
     }
-    const int lev = lv - 1;
-    const int Ln = lev + 1;
-    if (kCount) r.n_reads += (uint32_t)(Ln - lstar);
-    uint2 nval = make_uint2(0u, 0u);
-    if (slot < 0) {
-        nval = load_leaf(T, prec, kk, slot);
-        if (kCount) r.n_leaf += 1;
-    }
-    const bool rebase = fexit || (Ln - r.f > P.frame_levels);
-    // 4. precision of this boundary
+    // 4. precision of this boundary (past the canvas: a boundary to sigma = 0)
     if (!have64) {
         if (rebase) {
             need64();
@@ -584,13 +590,13 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     }
     // 5. composite the current leaf, then terminate or advance
     composite(r, teh, tel);
-    if (r.T < P.t_min) {
-        finish(r, P);
-        return false;
-    }
-    if (r.steps >= P.step_limit) {
+    bool end = leaves_canvas || r.T < P.t_min;
+    if (!end && r.steps >= P.step_limit) {
         atomicOr(&P.scratch->status, 1ull);
         atomicAdd(&P.scratch->stats[kStatStepLimited], 1ull);
+        end = true;
+    }
+    if (end) {
         finish(r, P);
         return false;
     }

@@ -53,7 +53,9 @@ struct PlainCount {
     unsigned long long steps, leaf_loads, rec_loads;
 };
 
-template <typename R>
+// kWrap: the canvas has more than 2^31 leaves (slots hold leaf numbers modulo 2^31); an instance
+// without it reads the number straight from the slot.
+template <typename R, bool kWrap>
 __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long idx) {
     using N = Num<R>;
     const View& V = *P.view;
@@ -100,10 +102,10 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
             unsigned cc[3] = {0u, 0u, 0u};
             int lev = 0;
             int32_t rec = 0, slot;
-            int k = 0;
+            int64_t li = 0;  // number of the located leaf (slot < 0)
             for (;;) {
                 const R w = E * N::pow2(-(lev + 1));
-                k = 0;
+                int k = 0;
                 for (int a = 0; a < 3; ++a) {
                     const R M = N::fma_((R)(2u * cc[a] + 1u), w, -half);
                     unsigned b;
@@ -122,6 +124,7 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
                     rec = slot;
                     ++lev;
                 } else {
+                    if (slot < 0) li = kWrap ? leaf_index(T, rec, k, slot) : -(int64_t)slot - 1;
                     break;
                 }
             }
@@ -138,7 +141,6 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
             te = fmin(te, t1);
             steps += 1;
             if (slot < 0) {
-                const int64_t li = leaf_index(T, rec, k, slot);
                 const uint2 q = __ldg(T.leaves + li);
                 leaf_loads += 1;
                 if (P.mark_leaf) mark_bit(P.mark_leaf, li);
@@ -167,12 +169,12 @@ __device__ __forceinline__ PlainCount plain_ray(const PlainParams& P, long long 
     return PlainCount{(unsigned long long)steps, leaf_loads, rec_loads};
 }
 
-template <typename R>
+template <typename R, bool kWrap>
 __global__ void __launch_bounds__(256) plain_kernel(PlainParams P, long long n_pixels) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     PlainCount c = {0ull, 0ull, 0ull};
     const bool valid = idx < n_pixels;
-    if (valid) c = plain_ray<R>(P, idx);
+    if (valid) c = plain_ray<R, kWrap>(P, idx);
     // counters in canvox_stats order: rays, steps, slot reads (not tracked here), leaf loads, record loads
     unsigned long long vals[5] = {valid ? 1ull : 0ull, c.steps, 0ull, c.leaf_loads, c.rec_loads};
     for (int q = 0; q < 5; ++q) {
@@ -295,8 +297,14 @@ cudaError_t launch_plain(const PlainParams& p, int precision, long long n_pixels
     const int block = 256;
     const long long grid = (n_pixels + block - 1) / block;
     if (grid > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-    if (precision == CANVOX_PREC_FP32) plain_kernel<float><<<(unsigned)grid, block, 0, s>>>(p, n_pixels);
-    else plain_kernel<double><<<(unsigned)grid, block, 0, s>>>(p, n_pixels);
+    const bool wrap = p.tree.n_wrap > 0;
+    if (precision == CANVOX_PREC_FP32) {
+        if (wrap) plain_kernel<float, true><<<(unsigned)grid, block, 0, s>>>(p, n_pixels);
+        else plain_kernel<float, false><<<(unsigned)grid, block, 0, s>>>(p, n_pixels);
+    } else {
+        if (wrap) plain_kernel<double, true><<<(unsigned)grid, block, 0, s>>>(p, n_pixels);
+        else plain_kernel<double, false><<<(unsigned)grid, block, 0, s>>>(p, n_pixels);
+    }
     return cudaGetLastError();
 }
 
