@@ -401,7 +401,7 @@ def main():
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": ctr["dram_bytes_per_launch"] if ctr else None, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": algo_bytes, "bytes_formula": "32*slot_reads + 8*leaf_loads + 16*rays",
-            "bound_note": "what binds is instruction issue (ncu: ~71 % of issue slots busy, ALU the busiest pipe, "
+            "bound_note": "what binds is instruction issue (ncu: 0.84 of the issue peak on this launch, ALU the busiest pipe, "
                           "DRAM ~0.2 % of the algorithmic bytes): see 'issue'; the gathers are served by L1/L2",
         }
         if ctr:

@@ -301,6 +301,10 @@ __device__ __forceinline__ uint32_t side64(const Ray& r, const Tree& T, int a, u
     return high64(r, a, M, t);
 }
 
+// Frame level for a leaf at level L that has descended past its frame: the level depth - K that holds the
+// canvas's deepest leaves within K levels, kept within [L - K, L].
+__device__ __forceinline__ int deep_frame(int L, int depth, int K) { return max(L - K, min(max(0, depth - K), L)); }
+
 // Start ray g of the launch. Returns true if it has a leaf to step from.
 template <bool kSmem, bool kRopes, bool kCount>
 __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsigned long long g, int32_t* stk) {
@@ -434,7 +438,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
     }
     r.steps = 1;
     if (r.L - r.f > P.frame_levels) {
-        r.f = r.L - P.frame_levels;
+        r.f = deep_frame(r.L, T.depth, P.frame_levels);
         set_frame(r, T, inv_extent, t0);
     }
     return true;
@@ -506,7 +510,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     int32_t prec = 0;
     int kk = 0;
     uint2 nval = make_uint2(0u, 0u);  // the next leaf's value (empty past the canvas)
-    bool rebase = false;
+    bool rebase = false, frame_exit = false;
     if (!leaves_canvas) {
         const int lstar = r.L - (32 - __clz(cold ^ cn));
         const bool fexit = lstar < r.f;
@@ -577,6 +581,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
             if (kCount) r.n_leaf += 1;
         }
         rebase = fexit || (Ln - r.f > P.frame_levels);
+        frame_exit = fexit;
     }
     // 4. precision of this boundary (past the canvas: a boundary to sigma = 0)
     if (!have64) {
@@ -612,7 +617,9 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     }
     r.steps += 1;
     if (rebase) {
-        r.f = max(0, Ln - P.frame_levels);
+        // a frame exit takes the coarsest frame that holds the new leaf; a descent past the frame the
+        // deepest one the canvas can need, so that deeper leaves do not rebase again level by level
+        r.f = frame_exit ? max(0, Ln - P.frame_levels) : deep_frame(Ln, T.depth, P.frame_levels);
         set_frame(r, T, inv_extent, te64);
     } else {
         r.cur_hi = teh;
