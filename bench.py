@@ -250,59 +250,87 @@ def run_reference(args):
     return 0
 
 
+BUILTIN_SCHEDULE = {"tile_w": 8, "frame_levels": 20, "refill": 0, "block_threads": 256, "blocks_per_sm": 0,
+                    "smem_records": 0, "traversal": 0}
+
+
+def deep_oracle(samples):
+    """Spawned helper of deep_workloads (host cores only): the host painter's pools of the depth-27 canvas and the
+    oracle on the sampled pixels of configs 3 and 4. Returns ({config: rgba [n, 4]}, host painter seconds)."""
+    import oracle
+    import synth
+    t = time.perf_counter()
+    canvas = synth.build_config(3)
+    host_s = time.perf_counter() - t
+    return {cid: oracle.render(canvas, synth.config_cameras(cid), px_idx=px) for cid, px in samples.items()}, host_s
+
+
 def deep_workloads(cx, synth, torch, stream, flush, dev, topts, steps=5):
     """The depth-27 canvas of 1,000,000 fine stamps (configs 3 and 4), painted on the GPU from its stamp table;
     config 3's eight stereo pairs in one persistent launch replayed from a CUDA graph, config 4's 64 uneven views
-    batched (one launch) and one launch per view. Max error against the oracle on seeded pixel samples, the
-    oracle reading the host painter's pools of the same stamps."""
-    import oracle
+    batched (one launch), one launch per view, with the built-in schedule and with the schedule the autotuner picks
+    for them. Max error against the oracle on seeded pixel samples; the oracle reads the host painter's pools of the
+    same stamps, built and rendered in a spawned process while the GPU is timed."""
+    import concurrent.futures
+    import multiprocessing
     out = {}
+    cams = {cid: synth.config_cameras(cid) for cid in (3, 4)}
+    samples = {}
+    for cid in (3, 4):
+        n_px = synth.total_pixels(cams[cid])
+        rng = np.random.default_rng(1704 + cid)
+        samples[cid] = np.sort(rng.choice(n_px, size=min(n_px, 200000), replace=False)).astype(np.int64)
+    pool = concurrent.futures.ProcessPoolExecutor(max_workers=1, mp_context=multiprocessing.get_context("spawn"))
+    fut = pool.submit(deep_oracle, samples)
     D, E, c, r, q, _ = synth.config_stamps(3)
     t = time.perf_counter()
     nr, nl = cx.paint_spheres(D, E, c, r, q)
     paint_s = time.perf_counter() - t
-    canvas = None
-    for cid in (3, 4):
-        cams = synth.config_cameras(cid)
-        n_px = synth.total_pixels(cams)
-        img = torch.empty((n_px, 4), dtype=torch.float32, device=dev)
-        runs = {"graph": dict(topts, use_graph=1)} if cid == 3 else \
-            {"batched": dict(topts), "per_view": dict(topts, per_view=1)}
-        res = {}
-        for name, o in runs.items():
-            for _ in range(3):
-                cx.render(cams, img, **o)
+
+    def timed(cid, o):
+        img = torch.empty((synth.total_pixels(cams[cid]), 4), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            cx.render(cams[cid], img, **o)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cx.render(cams[cid], img, **o)
+            e1.record(stream)
             torch.cuda.synchronize()
-            ms = []
-            for _ in range(steps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                cx.render(cams, img, **o)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            res[name] = {"Mrays_s": n_px / (statistics.median(ms) * 1e-3) / 1e6, "ms": statistics.median(ms)}
-        host = img.cpu().numpy().astype(np.float64)   # the last run's image (graph / per-view launches)
-        if canvas is None:
-            t = time.perf_counter()
-            canvas = synth.build_config(3)
-            host_s = time.perf_counter() - t
-        rng = np.random.default_rng(1704 + cid)
-        px = np.sort(rng.choice(n_px, size=min(n_px, 200000), replace=False)).astype(np.int64)
-        ref = oracle.render(canvas, cams, px_idx=px)
-        err = np.abs(host[px] - ref).max(axis=1)
-        key = "c3" if cid == 3 else "c4"
-        out[key] = {"workload": synth.CONFIGS[cid]["name"] + f" ({len(cams)} views, {n_px} rays, depth {D},"
-                                                               f" {nr} records, {nl} leaves)",
+            ms.append(e0.elapsed_time(e1))
+        m = statistics.median(ms)
+        sampled = img[torch.from_numpy(samples[cid]).to(dev)].cpu().numpy().astype(np.float64)
+        return {"Mrays_s": img.shape[0] / (m * 1e-3) / 1e6, "ms": m}, sampled
+
+    res3, img3 = timed(3, dict(topts, use_graph=1))
+    res4 = {}
+    res4["batched"], img4 = timed(4, dict(topts))
+    res4["per_view"], _ = timed(4, dict(topts, per_view=1))
+    res4["builtin_schedule"], _ = timed(4, dict(topts, **BUILTIN_SCHEDULE))
+    t = time.perf_counter()
+    best = cx.autotune(cams[4])
+    tune_s = time.perf_counter() - t
+    tuned = {k: best[k] for k in BUILTIN_SCHEDULE}
+    res4["autotuned_on_c4"], _ = timed(4, dict(topts, **tuned))
+    refs, host_s = fut.result()
+    pool.shutdown()
+    for cid, res, img in ((3, {"graph": res3}, img3), (4, res4, img4)):
+        err = np.abs(img - refs[cid]).max(axis=1)
+        key = f"c{cid}"
+        out[key] = {"workload": synth.CONFIGS[cid]["name"] + f" ({len(cams[cid])} views, {synth.total_pixels(cams[cid])}"
+                                                               f" rays, depth {D}, {nr} records, {nl} leaves)",
                     "timings": res, "max_err_vs_oracle": float(err.max()), "pixels_over_1e-5": int(np.sum(err > 1e-5)),
-                    "oracle_pixels": int(px.size), "l2": "flushed before every timed render"}
-        if cid == 3:
-            out[key]["stereo_fps"] = 8 / (res["graph"]["ms"] * 1e-3)
-            out[key]["device_painter_seconds"] = round(paint_s, 2)
-            out[key]["host_painter_seconds"] = round(host_s, 1)
-        else:
-            out[key]["batched_over_per_view"] = res["per_view"]["ms"] / res["batched"]["ms"]
+                    "oracle_pixels": int(samples[cid].size), "l2": "flushed before every timed render",
+                    "schedule": "the one autotuned on c2 unless the timing's name says otherwise"}
+    out["c3"]["stereo_fps"] = 8 / (res3["ms"] * 1e-3)
+    out["c3"]["device_painter_seconds"] = round(paint_s, 2)
+    out["c3"]["host_painter_seconds"] = round(host_s, 1)
+    out["c4"]["batched_over_per_view"] = res4["per_view"]["ms"] / res4["batched"]["ms"]
+    out["c4"]["autotuned_over_builtin"] = res4["builtin_schedule"]["ms"] / res4["autotuned_on_c4"]["ms"]
+    out["c4"]["autotune"] = dict(tuned, seconds=round(tune_s, 1))
     return out
 
 
