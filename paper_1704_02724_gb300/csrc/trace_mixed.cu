@@ -21,7 +21,10 @@
 // FP64 ray parameter where the frame was entered and S_f its size. This is the
 // paper's cell-local frame (origin at a cell, unit size) widened from one cell
 // to a subtree. The frame is re-anchored in FP64 whenever the ray leaves it, so
-// the drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames.
+// the drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames:
+// on a frame exit to the coarsest frame that holds the new leaf, on a descent
+// more than K levels below the frame to the frame depth - K (the deepest one
+// the canvas can need), so that a ray entering a deep region rebases once.
 // inv_d and nod_f are each kept as two FP32 words. Decisions (which face of the
 // leaf the ray leaves by, which side of a mid-plane it is on) are screened in
 // plain FP32 with a proven margin, and taken in FP64 from the exact planes when

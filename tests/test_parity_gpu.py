@@ -309,6 +309,20 @@ def test_schedules_agree_bitwise():
         np.testing.assert_array_equal(img, base, err_msg=str(kw))
 
 
+def test_read_counters_off_same_image():
+    """count_reads = 0 runs the kernel instance without the per-lane read counters: the same image bit for bit,
+    slot reads, leaf loads and record loads reported as 0, the other counters unchanged."""
+    cv = config_canvas(0)
+    cams = _edge_cameras(1.0)
+    a, sa = render(cv, cams, key="c0")
+    for kw in (dict(), dict(traversal=1), dict(smem_records=100)):
+        b, sb = render(cv, cams, key="c0", count_reads=0, **kw)
+        np.testing.assert_array_equal(a, b, err_msg=str(kw))
+        assert sb["slot_reads"] == sb["leaf_loads"] == sb["record_loads"] == 0
+        assert (sb["rays"], sb["steps"]) == (sa["rays"], sa["steps"])
+    assert sa["slot_reads"] > 0 and sa["leaf_loads"] > 0
+
+
 def test_frame_levels_do_not_change_depth27_pixels():
     """Frames of 1 to 22 levels give the same image within the bar on the depth-27 canvas (precision pin)."""
     cv = config_canvas(3)
