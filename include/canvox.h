@@ -196,8 +196,10 @@ int canvox_paint_spheres(int32_t depth, double extent, const double* centers, co
 /*
  * Add n stamps after those already painted and repaint (the editing path: only the new
  * stamps, 56 bytes each, cross the bus; the painter keeps the stamp table of the current
- * canvas in device memory). The result is the canvas canvox_paint_spheres would build
- * from the whole table. Needs a current canvas made by canvox_paint_spheres or this call
+ * canvas in device memory, and what it painted below level 5, per level-5 cell). Stamps
+ * added later never change what earlier ones did, so only the level-5 cells whose stamp
+ * lists the new stamps reach are painted again; the other cells' subtrees are kept. The
+ * result is the canvas canvox_paint_spheres would build from the whole table. Needs a current canvas made by canvox_paint_spheres or this call
  * (CANVOX_ERR_NOT_UPLOADED otherwise, e.g. after canvox_upload_octree). Same arguments,
  * errors and synchronisation as canvox_paint_spheres; on an argument error nothing changes.
  */

@@ -139,9 +139,14 @@ cudaError_t launch_rope_level(const int32_t* nodes, uint2* ropes, int64_t lo, in
 cudaError_t launch_eye_paths(const Tree& t, const View* views, int n_views, EyePath* out, cudaStream_t s);
 cudaError_t probe_l2_gather(int64_t buffer_bytes, double* gbs);
 cudaError_t probe_fp64(double* gflops);
+// The device painter. *cache: what it keeps of the last painted canvas for appends (null: none). When it holds
+// the same depth and extent and the first stamps of this table, only the partitions whose stamp lists changed
+// are painted again; either way it is replaced by the new canvas's cache (null on failure).
+struct PaintCache;
+void paint_cache_free(PaintCache* c);
 cudaError_t paint_pools(int32_t depth, double extent, const double* d_centers, const double* d_radii, const float4* d_rgba,
-                        int64_t n, int32_t** d_nodes, uint2** d_leaves, int64_t* n_rec, int64_t* n_leaf,
-                        std::vector<int64_t>* level_begin, int64_t* wrap, int32_t* n_wrap);  // wrap: kMaxWraps
+                        int64_t n, PaintCache** cache, int32_t** d_nodes, uint2** d_leaves, int64_t* n_rec,
+                        int64_t* n_leaf, std::vector<int64_t>* level_begin, int64_t* wrap, int32_t* n_wrap);  // wrap: kMaxWraps
 cudaError_t scan_i64(int64_t* d, int64_t n, int64_t* total);
 cudaError_t footprint_finish(const int32_t* nodes, const int64_t* level_begin, int n_levels, uint32_t* rec_bits,
                              int64_t rec_words, const uint32_t* leaf_bits, int64_t leaf_words,

@@ -28,6 +28,7 @@
 // with each stamp's distances to the cell's three planes per axis shared by
 // the children. Geometry is FP64 with the
 // same operations and order as the host painter, so the pools are identical.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -750,6 +751,139 @@ struct DevBuf {
 
 unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// ---------------------------------------------------------------------------
+// Partitions for appends. The refined cells of one level P (the partition level)
+// split the tree: breadth-first order keeps each one's subtree contiguous within
+// every deeper level, in the order of the partitions. Stamps appended later do
+// not change what any earlier stamp does (a cell's first refining stamp can only
+// appear among the new ones), so a partition whose stamp list at level P is
+// unchanged keeps its whole subtree, and only the others are painted again.
+// ---------------------------------------------------------------------------
+
+// pid_next[child index] = pid[parent] for every internal child (the partition a cell belongs to).
+__global__ void pid_propagate(int64_t n, const uint64_t* slot, const int32_t* pid, int32_t* pid_next) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * n) return;
+    const uint64_t v = slot[t];
+    if (v & kInternal) pid_next[v & ~kInternal] = pid[t >> 3];
+}
+
+// off[p] = first index of partition p in the (nondecreasing) partition ids of one level, p = 0 .. nseg.
+__global__ void seg_offsets(int64_t n, const int32_t* pid, int64_t nseg, int64_t* off) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > nseg) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pid[mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    off[p] = lo;
+}
+
+__global__ void iota32(int64_t n, int32_t* v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)i;
+}
+
+// Morton code of a level-P cell: its child indices k = x + 2y + 4z from the root down, 3 bits per level (the
+// breadth-first order of the level).
+__device__ __forceinline__ uint64_t morton(const uint32_t* c, int P) {
+    uint64_t m = 0;
+    for (int b = P - 1; b >= 0; --b)
+        m = (m << 3) | (uint64_t)(((c[0] >> b) & 1u) | (((c[1] >> b) & 1u) << 1) | (((c[2] >> b) & 1u) << 2));
+    return m;
+}
+__global__ void morton_codes(int64_t n, const uint32_t* coord, int P, uint64_t* code) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) code[i] = morton(coord + 3 * i, P);
+}
+
+// One warp per new partition: the old partition with the same cell and the same stamp list (entry for entry),
+// else -1.
+__global__ void match_partitions(int64_t n_new, const uint32_t* coord_new, const int64_t* off_new,
+                                 const int32_t* ent_new, int64_t n_old, const uint64_t* code_old,
+                                 const int64_t* off_old, const int32_t* ent_old, int P, int32_t* reuse) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= n_new) return;  // warp-uniform
+    const uint64_t m = morton(coord_new + 3 * p, P);
+    int64_t lo = 0, hi = n_old;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (code_old[mid] < m) lo = mid + 1;
+        else hi = mid;
+    }
+    int32_t q = -1;
+    if (lo < n_old && code_old[lo] == m) {
+        const int64_t bn = off_new[p], en = off_new[p + 1], bo = off_old[lo], eo = off_old[lo + 1];
+        bool same = en - bn == eo - bo;
+        for (int64_t j = lane; same && j < en - bn; j += 32)
+            if (ent_new[bn + j] != ent_old[bo + j]) same = false;
+        same = __all_sync(kFullMask, same);
+        if (same) q = (int32_t)lo;
+    }
+    if (lane == 0) reuse[p] = q;
+}
+
+// Cells `sel` of a level (their coordinates and stamp lists) gathered into a new level; dst_off = exclusive scan of
+// the selected lists' lengths.
+__global__ void gather_cells(int64_t m, const int32_t* sel, const uint32_t* coord, const int64_t* off,
+                             const int32_t* ent, const int64_t* dst_off, uint32_t* ncoord, int64_t* noff, int32_t* nent) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= m) return;
+    const int64_t i = sel[r], b = off[i], e = off[i + 1], d = dst_off[r];
+    if (lane < 3) ncoord[3 * r + lane] = coord[3 * i + lane];
+    if (lane == 0) noff[r] = d;
+    for (int64_t j = lane; j < e - b; j += 32) nent[d + j] = ent[b + j];
+}
+__global__ void list_lengths(int64_t m, const int32_t* sel, const int64_t* off, int64_t* len) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < m) len[r] = off[sel[r] + 1] - off[sel[r]];
+}
+
+// Per new partition p, its cell count at one level: from the kept subtree (reuse[p] = q) or the repainted one
+// (rep[p] = r).
+__global__ void part_counts(int64_t n, const int32_t* reuse, const int32_t* rep, const int64_t* off_old,
+                            const int64_t* off_rep, int64_t* cnt) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t q = reuse[p];
+    cnt[p] = q >= 0 ? (off_old ? off_old[q + 1] - off_old[q] : 0) : (off_rep ? off_rep[rep[p] + 1] - off_rep[rep[p]] : 0);
+}
+
+// The assembled level: each cell's eight slots copied from its source, internal children renumbered to the
+// assembled next level (same partition, same position within it).
+__global__ void assemble_level(int64_t n_dst, int64_t n_part, const int64_t* dst_off, const int64_t* dst_off_next,
+                               const int32_t* reuse, const int32_t* rep, const uint64_t* slot_old,
+                               const int64_t* off_old, const int64_t* off_old_next, const uint64_t* slot_rep,
+                               const int64_t* off_rep, const int64_t* off_rep_next, uint64_t* slot_dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * n_dst) return;
+    const int64_t j = t >> 3;
+    int64_t lo = 0, hi = n_part;  // the partition p with dst_off[p] <= j < dst_off[p + 1]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (dst_off[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    const int64_t p = lo, local = j - dst_off[p];
+    const int32_t q = reuse[p];
+    uint64_t v;
+    int64_t src_next;
+    if (q >= 0) {
+        v = slot_old[8 * (off_old[q] + local) + (t & 7)];
+        src_next = (v & kInternal) ? off_old_next[q] : 0;
+    } else {
+        const int32_t r = rep[p];
+        v = slot_rep[8 * (off_rep[r] + local) + (t & 7)];
+        src_next = (v & kInternal) ? off_rep_next[r] : 0;
+    }
+    if (v & kInternal) v = kInternal | (uint64_t)((int64_t)(v & ~kInternal) - src_next + dst_off_next[p]);
+    slot_dst[t] = v;
+}
+
 }  // namespace
 
 #define PCK(call)                                    \
@@ -758,107 +892,14 @@ unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
         if (e_ != cudaSuccess) return e_;            \
     } while (0)
 
-cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const double* d_r, const float4* d_rgba,
-                        int64_t n, int32_t** d_nodes_out, uint2** d_leaves_out, int64_t* n_rec_out, int64_t* n_leaf_out,
-                        std::vector<int64_t>* level_begin, int64_t* wrap_out, int32_t* n_wrap_out) {
-    const double half = 0.5 * extent;
+namespace {
+
+// Merge of identical siblings and the breadth-first pools of the painted levels (slots[l]: 8 child slots per
+// refined cell of level l), with the positions where leaf numbers pass multiples of 2^31.
+cudaError_t finish_pools(const std::vector<uint64_t*>& slots, const std::vector<int64_t>& ncell, int32_t** d_nodes_out,
+                         uint2** d_leaves_out, int64_t* n_rec_out, int64_t* n_leaf_out,
+                         std::vector<int64_t>* level_begin, int64_t* wrap_out, int32_t* n_wrap_out) {
     DevBuf buf;
-    // squared radii and target depths (the host painter's integer loop, in the same FP64 operations)
-    double* d_r2;
-    int32_t* d_kt;
-    PCK(buf.alloc(&d_r2, n));
-    PCK(buf.alloc(&d_kt, n));
-    if (n > 0) {
-        stamp_prep<<<blocks_for(n, 256), 256>>>(d_r, n, depth, extent, d_r2, d_kt);
-        PCK(cudaGetLastError());
-    }
-    const StampDev S{d_c, d_r2, d_kt, d_rgba};
-    // level 0: the root and the stamps that touch the canvas
-    int64_t *flag, n_root = 0;
-    PCK(buf.alloc(&flag, n));
-    if (n > 0) {
-        root_flags<<<blocks_for(n, 256), 256>>>(S, n, extent, half, flag);
-        PCK(cudaGetLastError());
-    }
-    int64_t* flag_scan;
-    PCK(buf.alloc(&flag_scan, n));
-    if (n > 0) {
-        PCK(cudaMemcpy(flag_scan, flag, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice));
-        PCK(scan_i64(flag_scan, n, &n_root));
-    }
-    uint32_t* coord;
-    int64_t* off;
-    int32_t* ent;
-    PCK(buf.alloc(&coord, 3));
-    PCK(buf.alloc(&off, 2));
-    PCK(buf.alloc(&ent, n_root));
-    PCK(cudaMemset(coord, 0, 3 * sizeof(uint32_t)));
-    const int64_t off0[2] = {0, n_root};
-    PCK(cudaMemcpy(off, off0, sizeof(off0), cudaMemcpyHostToDevice));
-    if (n > 0) {
-        root_write<<<blocks_for(n, 256), 256>>>(n, flag_scan, flag, ent);
-        PCK(cudaGetLastError());
-    }
-    buf.release(flag);
-    buf.release(flag_scan);
-    // top-down: refined cells level by level, child slots kept for the output
-    std::vector<uint64_t*> slots;
-    std::vector<int64_t> ncell;
-    LevelIn L{1, 0, coord, off, ent};
-    for (;;) {
-        const int64_t nch = 8 * L.n;
-        int32_t* fr;
-        uint64_t* slot;
-        int64_t *cnt, *isint;
-        PCK(buf.alloc(&fr, nch));
-        PCK(buf.alloc(&slot, nch));
-        PCK(buf.alloc(&cnt, nch));
-        PCK(buf.alloc(&isint, nch));
-        const bool split = L.n < kSplitCells;  // few cells: a warp per child
-        if (split)
-            expand_child_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr,
-                                                                                        slot, cnt, isint);
-        else
-            expand_parent_count<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, depth, extent, half, fr,
-                                                                                         slot, cnt, isint);
-        PCK(cudaGetLastError());
-        int64_t n_ent = 0, n_next = 0;
-        PCK(scan_i64(cnt, nch, &n_ent));
-        PCK(scan_i64(isint, nch, &n_next));
-        slots.push_back(slot);
-        ncell.push_back(L.n);
-        if (n_next == 0) {
-            buf.release(fr);
-            buf.release(cnt);
-            buf.release(isint);
-            break;
-        }
-        uint32_t* ncoord;
-        int64_t* noff;
-        int32_t* nent;
-        PCK(buf.alloc(&ncoord, 3 * n_next));
-        PCK(buf.alloc(&noff, n_next + 1));
-        PCK(buf.alloc(&nent, n_ent));
-        PCK(cudaMemcpy(noff + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
-        if (split)
-            expand_child_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot, cnt,
-                                                                                        isint, ncoord, noff, nent);
-        else
-            expand_parent_write<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(L, S, extent, half, fr, slot,
-                                                                                         cnt, isint, ncoord, noff, nent);
-        PCK(cudaGetLastError());
-        PCK(cudaDeviceSynchronize());
-        buf.release(fr);
-        buf.release(cnt);
-        buf.release(isint);
-        buf.release(const_cast<uint32_t*>(L.coord));
-        buf.release(const_cast<int64_t*>(L.off));
-        buf.release(const_cast<int32_t*>(L.ent));
-        L = LevelIn{n_next, L.level + 1, ncoord, noff, nent};
-    }
-    buf.release(const_cast<uint32_t*>(L.coord));
-    buf.release(const_cast<int64_t*>(L.off));
-    buf.release(const_cast<int32_t*>(L.ent));
     // bottom-up merge of identical siblings
     const int nl = (int)slots.size();
     std::vector<uint64_t*> ckey((size_t)nl + 1, nullptr);
@@ -930,6 +971,387 @@ cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const d
     for (int l = 0; l <= nl; ++l)
         if (l == 0 || rec_base[(size_t)l] > rec_base[(size_t)l - 1]) level_begin->push_back(rec_base[(size_t)l]);
     return cudaSuccess;
+}
+
+}  // namespace
+
+namespace {
+
+// Refined cells of one level with their ordered stamp lists (device arrays owned here).
+struct Level {
+    int64_t n = 0;
+    int32_t level = 0;
+    uint32_t* coord = nullptr;  // [n][3]
+    int64_t* off = nullptr;     // [n + 1]
+    int32_t* ent = nullptr;     // s: descends, ~s: paints the whole cell
+    LevelIn in() const { return LevelIn{n, level, coord, off, ent}; }
+    void free() {
+        cudaFree(coord);
+        cudaFree(off);
+        cudaFree(ent);
+        coord = nullptr;
+        off = nullptr;
+        ent = nullptr;
+        n = 0;
+    }
+};
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t n) {
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+// Expand one level: the eight child slots of each cell (*slot_out, handed to the caller: a leaf key, or
+// kInternal | index in the next level) and the next level's refined cells with their lists.
+cudaError_t expand(const Level& L, const StampDev& S, int32_t depth, double extent, double half, uint64_t** slot_out,
+                   Level* next) {
+    DevBuf buf;
+    const int64_t nch = 8 * L.n;
+    int32_t* fr;
+    int64_t *cnt, *isint;
+    uint64_t* slot;
+    PCK(buf.alloc(&fr, nch));
+    PCK(buf.alloc(&cnt, nch));
+    PCK(buf.alloc(&isint, nch));
+    PCK(dalloc(&slot, nch));
+    *slot_out = slot;
+    const LevelIn in = L.in();
+    const bool split = L.n < kSplitCells;  // few cells: a warp per child
+    if (split)
+        expand_child_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, fr, slot,
+                                                                                    cnt, isint);
+    else
+        expand_parent_count<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, fr,
+                                                                                     slot, cnt, isint);
+    PCK(cudaGetLastError());
+    int64_t n_ent = 0, n_next = 0;
+    PCK(scan_i64(cnt, nch, &n_ent));
+    PCK(scan_i64(isint, nch, &n_next));
+    next->n = n_next;
+    next->level = L.level + 1;
+    if (n_next == 0) return cudaSuccess;  // no internal child: the slots are all leaf keys
+    PCK(dalloc(&next->coord, 3 * n_next));
+    PCK(dalloc(&next->off, n_next + 1));
+    PCK(dalloc(&next->ent, n_ent));
+    PCK(cudaMemcpy(next->off + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (split)
+        expand_child_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, slot, cnt,
+                                                                                    isint, next->coord, next->off,
+                                                                                    next->ent);
+    else
+        expand_parent_write<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, slot,
+                                                                                     cnt, isint, next->coord, next->off,
+                                                                                     next->ent);
+    PCK(cudaGetLastError());
+    return cudaDeviceSynchronize();
+}
+
+// Paint down from L (its arrays are freed on the way): slots and cell counts per level, until no refined cell is
+// left, or up to level `stop` (that level's cells are then left unexpanded in *rest). With track, the cells of L
+// are partitions 0 .. L.n - 1 and offs receives, per painted level, the first cell of each partition.
+cudaError_t paint_down(Level L, const StampDev& S, int32_t depth, double extent, double half, int stop, bool track,
+                       std::vector<uint64_t*>* slots, std::vector<int64_t>* ncell, Level* rest,
+                       std::vector<int64_t*>* offs) {
+    const int64_t nseg = L.n;
+    int32_t* pid = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (track && L.n > 0) {
+        e = dalloc(&pid, L.n);
+        if (e == cudaSuccess) iota32<<<blocks_for(L.n, 256), 256>>>(L.n, pid);
+    }
+    while (e == cudaSuccess && L.n > 0 && L.level != stop) {
+        uint64_t* slot = nullptr;
+        Level next;
+        e = expand(L, S, depth, extent, half, &slot, &next);
+        if (slot) {
+            slots->push_back(slot);
+            ncell->push_back(L.n);
+        }
+        if (e == cudaSuccess && track) {
+            int64_t* off = nullptr;
+            e = dalloc(&off, nseg + 1);
+            if (e == cudaSuccess) {
+                offs->push_back(off);
+                seg_offsets<<<blocks_for(nseg + 1, 256), 256>>>(L.n, pid, nseg, off);
+                int32_t* pid_next = nullptr;
+                if (next.n > 0 && (e = dalloc(&pid_next, next.n)) == cudaSuccess)
+                    pid_propagate<<<blocks_for(8 * L.n, 256), 256>>>(L.n, slot, pid, pid_next);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                cudaFree(pid);
+                pid = pid_next;
+            }
+        }
+        L.free();
+        L = next;
+        if (e != cudaSuccess) L.free();
+    }
+    cudaFree(pid);
+    if (e == cudaSuccess && L.n > 0 && L.level == stop) {
+        *rest = L;
+    } else {
+        L.free();
+        rest->n = 0;
+        rest->level = stop;
+    }
+    return e == cudaSuccess ? cudaDeviceSynchronize() : e;
+}
+
+}  // namespace
+
+// What the painter keeps of a painted canvas for appends: the level-P cells (Morton codes and stamp lists) and
+// the slots of every level from P down, with each partition's first cell per level.
+struct PaintCache {
+    int32_t depth = 0;
+    double extent = 0.0;
+    int64_t n_stamps = 0;       // stamps painted
+    int64_t nP = 0;             // refined cells at the partition level
+    uint64_t* code = nullptr;   // [nP] Morton codes (ascending)
+    int64_t* lst_off = nullptr; // [nP + 1]
+    int32_t* lst_ent = nullptr; // their stamp lists
+    std::vector<uint64_t*> slots;  // levels P, P + 1, ...
+    std::vector<int64_t> ncell;
+    std::vector<int64_t*> off;     // per level: [nP + 1] first cell of each partition
+};
+
+void paint_cache_free(PaintCache* c) {
+    if (!c) return;
+    cudaFree(c->code);
+    cudaFree(c->lst_off);
+    cudaFree(c->lst_ent);
+    for (auto* p : c->slots) cudaFree(p);
+    for (auto* p : c->off) cudaFree(p);
+    delete c;
+}
+
+namespace {
+
+constexpr int kPartLevel = 5;  // partition level: up to 32,768 partitions
+
+void free_all(std::vector<uint64_t*>& v) {
+    for (auto* p : v) cudaFree(p);
+    v.clear();
+}
+void free_all(std::vector<int64_t*>& v) {
+    for (auto* p : v) cudaFree(p);
+    v.clear();
+}
+
+// The root with the stamps [0, n) that touch the canvas, in order.
+cudaError_t root_level(const StampDev& S, int64_t n, double extent, double half, Level* root) {
+    DevBuf buf;
+    int64_t *flag, *flag_scan, n_root = 0;
+    PCK(buf.alloc(&flag, n));
+    PCK(buf.alloc(&flag_scan, n));
+    if (n > 0) {
+        root_flags<<<blocks_for(n, 256), 256>>>(S, n, extent, half, flag);
+        PCK(cudaGetLastError());
+        PCK(cudaMemcpy(flag_scan, flag, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice));
+        PCK(scan_i64(flag_scan, n, &n_root));
+    }
+    root->n = 1;
+    root->level = 0;
+    PCK(dalloc(&root->coord, 3));
+    PCK(dalloc(&root->off, 2));
+    PCK(dalloc(&root->ent, n_root));
+    PCK(cudaMemset(root->coord, 0, 3 * sizeof(uint32_t)));
+    const int64_t off0[2] = {0, n_root};
+    PCK(cudaMemcpy(root->off, off0, sizeof(off0), cudaMemcpyHostToDevice));
+    if (n > 0) {
+        root_write<<<blocks_for(n, 256), 256>>>(n, flag_scan, flag, root->ent);
+        PCK(cudaGetLastError());
+    }
+    return cudaDeviceSynchronize();
+}
+
+// Per-level partition offsets and slots of the appended canvas, from the kept subtrees (reuse[p] >= 0) and the
+// repainted ones (rep[p] >= 0).
+cudaError_t assemble(int64_t n_part, const int32_t* reuse, const int32_t* rep, const PaintCache& old,
+                     const std::vector<uint64_t*>& slots_r, const std::vector<int64_t*>& offs_r,
+                     std::vector<uint64_t*>* slots, std::vector<int64_t>* ncell, std::vector<int64_t*>* offs) {
+    DevBuf buf;
+    int64_t* cnt;
+    PCK(buf.alloc(&cnt, n_part));
+    const size_t depth_max = std::max(old.slots.size(), slots_r.size());
+    for (size_t d = 0; d < depth_max; ++d) {
+        part_counts<<<blocks_for(n_part, 256), 256>>>(n_part, reuse, rep, d < old.off.size() ? old.off[d] : nullptr,
+                                                      d < offs_r.size() ? offs_r[d] : nullptr, cnt);
+        PCK(cudaGetLastError());
+        int64_t* off;
+        PCK(dalloc(&off, n_part + 1));
+        offs->push_back(off);
+        PCK(cudaMemcpy(off, cnt, sizeof(int64_t) * (size_t)n_part, cudaMemcpyDeviceToDevice));
+        int64_t total = 0;
+        PCK(scan_i64(off, n_part, &total));
+        PCK(cudaMemcpy(off + n_part, &total, sizeof(int64_t), cudaMemcpyHostToDevice));
+        if (total == 0) {
+            cudaFree(off);
+            offs->pop_back();
+            break;
+        }
+        ncell->push_back(total);
+    }
+    for (size_t d = 0; d < ncell->size(); ++d) {
+        uint64_t* slot;
+        PCK(dalloc(&slot, 8 * (*ncell)[d]));
+        slots->push_back(slot);
+        const bool last = d + 1 == ncell->size();
+        assemble_level<<<blocks_for(8 * (*ncell)[d], 256), 256>>>(
+            (*ncell)[d], n_part, (*offs)[d], last ? nullptr : (*offs)[d + 1], reuse, rep,
+            d < old.slots.size() ? old.slots[d] : nullptr, d < old.off.size() ? old.off[d] : nullptr,
+            d + 1 < old.off.size() ? old.off[d + 1] : nullptr, d < slots_r.size() ? slots_r[d] : nullptr,
+            d < offs_r.size() ? offs_r[d] : nullptr, d + 1 < offs_r.size() ? offs_r[d + 1] : nullptr, slot);
+        PCK(cudaGetLastError());
+    }
+    return cudaDeviceSynchronize();
+}
+
+}  // namespace
+
+cudaError_t paint_pools(int32_t depth, double extent, const double* d_c, const double* d_r, const float4* d_rgba,
+                        int64_t n, PaintCache** cache, int32_t** d_nodes_out, uint2** d_leaves_out, int64_t* n_rec_out,
+                        int64_t* n_leaf_out, std::vector<int64_t>* level_begin, int64_t* wrap_out,
+                        int32_t* n_wrap_out) {
+    const double half = 0.5 * extent;
+    PaintCache* old = *cache;
+    *cache = nullptr;
+    // an append: the same canvas, and the stamps the cache was painted with come first in the table
+    const bool append = old && old->depth == depth && old->extent == extent && old->n_stamps <= n;
+    DevBuf buf;
+    // squared radii and target depths (the host painter's integer loop, in the same FP64 operations)
+    double* d_r2;
+    int32_t* d_kt;
+    cudaError_t e = buf.alloc(&d_r2, n);
+    if (e == cudaSuccess) e = buf.alloc(&d_kt, n);
+    if (e == cudaSuccess && n > 0) {
+        stamp_prep<<<blocks_for(n, 256), 256>>>(d_r, n, depth, extent, d_r2, d_kt);
+        e = cudaGetLastError();
+    }
+    const StampDev S{d_c, d_r2, d_kt, d_rgba};
+    // levels 0 .. P - 1 from the root (always painted: every stamp reaches the root's list)
+    std::vector<uint64_t*> slots_top, slots_bot, slots_r;
+    std::vector<int64_t> ncell_top, ncell_bot, ncell_r;
+    std::vector<int64_t*> offs_bot, offs_r;
+    Level root, partP, rep_lvl, unused;
+    PaintCache* nc = nullptr;
+    if (e == cudaSuccess) e = root_level(S, n, extent, half, &root);
+    if (e == cudaSuccess) e = paint_down(root, S, depth, extent, half, kPartLevel, false, &slots_top, &ncell_top, &partP, nullptr);
+    else root.free();
+    if (e == cudaSuccess) {
+        nc = new PaintCache();
+        nc->depth = depth;
+        nc->extent = extent;
+        nc->n_stamps = n;
+        nc->nP = partP.n;
+        e = dalloc(&nc->code, partP.n);
+        if (e == cudaSuccess && partP.n > 0) {
+            morton_codes<<<blocks_for(partP.n, 256), 256>>>(partP.n, partP.coord, kPartLevel, nc->code);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && !append) {
+        // a full paint: every partition painted, a copy of their lists kept
+        Level start = partP;
+        int64_t* keep_off = nullptr;
+        int32_t* keep_ent = nullptr;
+        e = dalloc(&keep_off, partP.n + 1);
+        if (e == cudaSuccess) e = dalloc(&keep_ent, 1);
+        if (e == cudaSuccess && partP.n > 0) {
+            int64_t n_ent = 0;
+            e = cudaMemcpy(&n_ent, partP.off + partP.n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+            cudaFree(keep_ent);
+            keep_ent = nullptr;
+            if (e == cudaSuccess) e = dalloc(&keep_ent, n_ent);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(keep_ent, partP.ent, sizeof(int32_t) * (size_t)n_ent, cudaMemcpyDeviceToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(keep_off, partP.off, sizeof(int64_t) * (size_t)(partP.n + 1), cudaMemcpyDeviceToDevice);
+        }
+        nc->lst_off = keep_off;
+        nc->lst_ent = keep_ent;
+        if (e == cudaSuccess)
+            e = paint_down(start, S, depth, extent, half, -1, true, &slots_bot, &ncell_bot, &unused, &offs_bot);
+        else
+            start.free();
+        partP = Level();
+    } else if (e == cudaSuccess) {
+        // an append: keep the partitions whose cell and stamp list are unchanged, paint the others again
+        int32_t *reuse = nullptr, *rep = nullptr, *sel = nullptr;
+        int64_t* len = nullptr;
+        const int64_t np = partP.n;
+        std::vector<int32_t> h_reuse((size_t)np), h_rep((size_t)np, -1), h_sel;
+        e = buf.alloc(&reuse, np);
+        if (e == cudaSuccess && np > 0) {
+            match_partitions<<<blocks_for(32 * np, 256), 256>>>(np, partP.coord, partP.off, partP.ent, old->nP, old->code,
+                                                                old->lst_off, old->lst_ent, kPartLevel, reuse);
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h_reuse.data(), reuse, sizeof(int32_t) * (size_t)np, cudaMemcpyDeviceToHost);
+        }
+        for (int64_t p = 0; p < np; ++p)
+            if (h_reuse[(size_t)p] < 0) {
+                h_rep[(size_t)p] = (int32_t)h_sel.size();
+                h_sel.push_back((int32_t)p);
+            }
+        const int64_t m = (int64_t)h_sel.size();
+        if (e == cudaSuccess) e = buf.alloc(&rep, np);
+        if (e == cudaSuccess) e = buf.alloc(&sel, m);
+        if (e == cudaSuccess) e = buf.alloc(&len, m + 1);
+        if (e == cudaSuccess && np > 0) e = cudaMemcpy(rep, h_rep.data(), sizeof(int32_t) * (size_t)np, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && m > 0) e = cudaMemcpy(sel, h_sel.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice);
+        // the repainted partitions as one level
+        rep_lvl.n = m;
+        rep_lvl.level = kPartLevel;
+        if (e == cudaSuccess && m > 0) {
+            list_lengths<<<blocks_for(m, 256), 256>>>(m, sel, partP.off, len);
+            int64_t n_ent = 0;
+            e = scan_i64(len, m, &n_ent);
+            if (e == cudaSuccess) e = cudaMemcpy(len + m, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = dalloc(&rep_lvl.coord, 3 * m);
+            if (e == cudaSuccess) e = dalloc(&rep_lvl.off, m + 1);
+            if (e == cudaSuccess) e = dalloc(&rep_lvl.ent, n_ent);
+            if (e == cudaSuccess) {
+                gather_cells<<<blocks_for(32 * m, 256), 256>>>(m, sel, partP.coord, partP.off, partP.ent, len,
+                                                               rep_lvl.coord, rep_lvl.off, rep_lvl.ent);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpy(rep_lvl.off + m, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess)
+            e = paint_down(rep_lvl, S, depth, extent, half, -1, true, &slots_r, &ncell_r, &unused, &offs_r);
+        else
+            rep_lvl.free();
+        if (e == cudaSuccess) e = assemble(np, reuse, rep, *old, slots_r, offs_r, &slots_bot, &ncell_bot, &offs_bot);
+        free_all(slots_r);
+        free_all(offs_r);
+        // the new level-P lists are kept
+        nc->lst_off = partP.off;
+        nc->lst_ent = partP.ent;
+        cudaFree(partP.coord);
+        partP = Level();
+    }
+    paint_cache_free(old);
+    if (e == cudaSuccess) {
+        std::vector<uint64_t*> all(slots_top);
+        all.insert(all.end(), slots_bot.begin(), slots_bot.end());
+        std::vector<int64_t> cells(ncell_top);
+        cells.insert(cells.end(), ncell_bot.begin(), ncell_bot.end());
+        e = finish_pools(all, cells, d_nodes_out, d_leaves_out, n_rec_out, n_leaf_out, level_begin, wrap_out, n_wrap_out);
+    }
+    free_all(slots_top);
+    partP.free();
+    if (e == cudaSuccess) {
+        nc->slots = slots_bot;
+        nc->ncell = ncell_bot;
+        nc->off = offs_bot;
+        *cache = nc;
+    } else {
+        free_all(slots_bot);
+        free_all(offs_bot);
+        paint_cache_free(nc);
+    }
+    return e;
 }
 
 }  // namespace canvox

@@ -75,6 +75,7 @@ struct Ctx {
     float4* d_st_rgba = nullptr;
     int64_t st_n = 0, st_cap = 0;
     bool painted = false;
+    PaintCache* paint_cache = nullptr;  // the painter's state of the current painted canvas (for appends)
     // views: device table and two pinned staging buffers, each guarded by an event
     View* d_views = nullptr;
     EyePath* d_eye = nullptr;
@@ -452,8 +453,8 @@ int paint_table(int32_t depth, double extent, int64_t* n_records, int64_t* n_lea
     std::vector<int64_t> lb;
     int64_t wraps[kMaxWraps] = {};
     int32_t n_wrap = 0;
-    CK(paint_pools(depth, extent, g.d_st_c, g.d_st_r, g.d_st_rgba, g.st_n, &nodes, &leaves, &nr, &nl, &lb, wraps,
-                   &n_wrap),
+    CK(paint_pools(depth, extent, g.d_st_c, g.d_st_r, g.d_st_rgba, g.st_n, &g.paint_cache, &nodes, &leaves, &nr, &nl, &lb,
+                   wraps, &n_wrap),
        "device painter (or a canvas beyond 2^31 - 1 records / 2^34 leaves)");
     g.d_nodes = nodes;
     g.d_leaves = leaves;
@@ -557,6 +558,8 @@ int canvox_upload_octree(const int32_t* node_pool, int64_t n_records, const uint
     if (rc) return rc;
     // replace the device copy
     if ((rc = drop_canvas())) return rc;
+    paint_cache_free(g.paint_cache);  // an uploaded canvas cannot be appended to
+    g.paint_cache = nullptr;
     CK(cudaMalloc(&g.d_nodes, sizeof(int32_t) * 8 * (size_t)n_records), "cudaMalloc(nodes)");
     CK(cudaMalloc(&g.d_leaves, sizeof(uint2) * (size_t)(n_leaves > 0 ? n_leaves : 1)), "cudaMalloc(leaves)");
     CK(cudaMemcpy(g.d_nodes, node_pool, sizeof(int32_t) * 8 * (size_t)n_records, cudaMemcpyHostToDevice), "cudaMemcpy(nodes)");
@@ -596,6 +599,8 @@ int canvox_paint_spheres(int32_t depth, double extent, const double* centers, co
     if ((rc = check_canvas_args(depth, extent))) return rc;
     if ((rc = ensure_device())) return rc;
     if ((rc = drop_canvas())) return rc;
+    paint_cache_free(g.paint_cache);  // a new stamp table: painted whole
+    g.paint_cache = nullptr;
     if ((rc = reserve_stamps(n, 0))) return rc;
     if (n > 0) {
         CK(cudaMemcpy(g.d_st_c, centers, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice), "cudaMemcpy(stamps)");
@@ -991,6 +996,7 @@ void canvox_release(void) {
     if (g.d_st_c) cudaFree(g.d_st_c);
     if (g.d_st_r) cudaFree(g.d_st_r);
     if (g.d_st_rgba) cudaFree(g.d_st_rgba);
+    paint_cache_free(g.paint_cache);
     if (g.done) cudaEventDestroy(g.done);
     g = Ctx();
 }

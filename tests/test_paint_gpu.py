@@ -94,6 +94,53 @@ def test_paint_append_equals_whole_table():
     _uploaded["key"] = None
 
 
+@pytest.mark.parametrize("seed,D", [(11, 3), (12, 7), (13, 12), (14, 20)])
+def test_paint_append_in_chunks(seed, D):
+    """Appends repaint only the partitions (refined cells of level 5) whose stamp lists change: stamps appended
+    in chunks, among them one covering the whole canvas, some outside it, repeats of earlier stamps and an empty
+    append, give the host painter's pools of the whole table byte for byte after every chunk."""
+    rng = np.random.default_rng(seed)
+    E = [1.0, 3.0, 1000.0, 40000.0][seed % 4]
+    n = 400
+    c = rng.uniform(-0.6, 0.6, (n, 3)) * E
+    r = E * np.exp(rng.uniform(math.log(2.0 ** -(D + 1)), math.log(0.3), n))
+    q = np.c_[rng.uniform(0, 1, (n, 3)), rng.uniform(0, 30, n)].astype(np.float32)
+    c[300:310] = c[:10]                    # the same spheres again, later
+    r[300:310] = r[:10]
+    c[320] = (0.0, 0.0, 0.0)
+    r[320] = 2.0 * E                       # covers the whole canvas
+    c[330] = (5.0 * E, 0.0, 0.0)           # outside
+    _uploaded["key"] = None
+    cuts = [0, 150, 150, 290, 321, 331, 400]
+    cx.paint_spheres(D, E, c[:cuts[1]], r[:cuts[1]], q[:cuts[1]])
+    for a, b in zip(cuts[1:-1], cuts[2:]):
+        nr, nl = cx.paint_append(c[a:b], r[a:b], q[a:b])
+        ref = synth.stamp_canvas(D, E, c[:b], r[:b], q[:b])
+        assert (nr, nl) == (ref.n_records, ref.n_leaves), (a, b)
+        nodes, leaves = cx.download_octree()
+        np.testing.assert_array_equal(nodes, ref.nodes)
+        np.testing.assert_array_equal(leaves, ref.leaves)
+    h, d = cx.octree_hash()
+    assert h == d
+    _uploaded["key"] = None
+
+
+def test_paint_append_reduced_c2_localised():
+    """The editing case the append is for: the last stamps of a room appended to the depth-24 canvas painted from
+    the others (only the partition around that room is painted again), pools equal to the host painter's."""
+    D, E, c, r, q, _ = synth.config_stamps(2, n_fine=4000)
+    k = r.shape[0] - 100
+    _uploaded["key"] = None
+    cx.paint_spheres(D, E, c[:k], r[:k], q[:k])
+    nr, nl = cx.paint_append(c[k:], r[k:], q[k:])
+    ref = synth.stamp_canvas(D, E, c, r, q)
+    assert (nr, nl) == (ref.n_records, ref.n_leaves)
+    nodes, leaves = cx.download_octree()
+    np.testing.assert_array_equal(nodes, ref.nodes)
+    np.testing.assert_array_equal(leaves, ref.leaves)
+    _uploaded["key"] = None
+
+
 def test_paint_ties_on_cell_planes():
     """Stamps whose spheres touch cell faces, corners and centres exactly (distances equal to the radius) and whose
     radius puts r/10 exactly on a cell size: every comparison of the painter meets its tie."""
