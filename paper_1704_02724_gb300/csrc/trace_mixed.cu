@@ -60,8 +60,6 @@ constexpr float kEps21 = 4.76837158203125e-07f;     // 2^-21
 constexpr float kEps22 = 2.384185791015625e-07f;    // 2^-22
 constexpr float kEps41 = 4.547473508864641e-13f;    // 2^-41
 constexpr float kBigF = 1.0e37f;                    // stands for the time of a face the ray never meets (d_a = 0)
-constexpr float kEps42 = 2.2737367544323206e-13f;   // 2^-42
-constexpr float kOneMinus20 = 0.99999904632568359f; // 1 - 2^-20
 
 // Resident 256-thread blocks per SM the register allocation must allow (occupancy knob).
 #ifndef CANVOX_MIN_BLOCKS
@@ -134,10 +132,11 @@ static_assert(sizeof(Cold) == 88, "per-lane shared record: 88 bytes keeps four b
 
 struct Ray {
     Cold* k;
-    float ih[3], il[3];         // inv_d as two FP32 words (0 for d = 0)
-    float nh[3], nl[3];         // frame-local nod (for d = 0: the position) as two FP32 words
+    float ih[3], il[3];         // inv_d as two FP32 words; for d_a = 0 the frame-local position, low word in ih
+    float nh[3], nl[3];         // frame-local nod as two FP32 words; for d_a = 0: kBigF and 0, so that the far
+                                // face of that axis evaluates to the time kBigF with no test
     float sf, sf_eps;           // frame size, frame size * 2^-43
-    float gscr;                 // 2^-41 max_a (|ih_a| + |nh_a|): double-float part of the exit screen's margin
+    float gscr;                 // 2^-41 max (|ih_a| + |nh_a|) over the axes with d_a != 0: the screens' margin term
     float cur_hi, cur_lo;       // frame-local parameter of the current leaf's entry
     float2* acc;  // shared, stride kBlock: (sum, Kahan term) of the colour channels 0, 1, 2
     float* err;   // shared: colour-error bound spent so far (the budget of the FP32 boundaries)
@@ -218,10 +217,18 @@ __device__ __forceinline__ void set_frame(Ray& r, const Tree& T, double inv_exte
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double Fmin = fma((double)(r.c[a] >> sh), Sf, -T.half);
-        const double n = is_zero(r, a) ? (r.k->nod64[a] - Fmin) * r.k->invS : (fma(Fmin, r.k->inv64[a], r.k->nod64[a]) - t) * r.k->invS;
-        r.nh[a] = (float)n;
-        r.nl[a] = (float)(n - (double)r.nh[a]);
-        g = fmaxf(g, __fadd_rn(fabsf(r.ih[a]), fabsf(r.nh[a])));
+        if (is_zero(r, a)) {
+            const double n = (r.k->nod64[a] - Fmin) * r.k->invS;
+            r.il[a] = (float)n;
+            r.ih[a] = (float)(n - (double)r.il[a]);
+            r.nh[a] = kBigF;
+            r.nl[a] = 0.0f;
+        } else {
+            const double n = (fma(Fmin, r.k->inv64[a], r.k->nod64[a]) - t) * r.k->invS;
+            r.nh[a] = (float)n;
+            r.nl[a] = (float)(n - (double)r.nh[a]);
+            g = fmaxf(g, __fadd_rn(fabsf(r.ih[a]), fabsf(r.nh[a])));
+        }
     }
     r.gscr = __fmul_rn(kEps41, g);
     r.sf = (float)Sf;
@@ -274,25 +281,27 @@ __device__ __forceinline__ void finish(Ray& r, const MixedParams& P) {
 //     F = fl(fl(Mp ih + nh) + fl(Mp il + nl))        (Mp <= 1: a frame plane)
 // is within 2^-23 |F| + 2^-47 (|ih| + |nh|) of the exact time, and the
 // difference D = fl(fl(F - th) - tl) within 2^-23 (|F| + |th| + |D|) more.
-// When |D| exceeds 2^-21 (|F| + |th|) + 2^-42 (|ih| + |nh|) + margin_t (with
-// room for its own rounding) the side is the sign of D. Otherwise, and for
+// The side is the sign of D when
+//     |D| > fl(2^-21 |F| + base),   base = fl(2^-21 |th| + fl(gscr + margin_t))
+// (the caller forms base once per leaf step). Its 2^-21 is twice the 2^-22 that
+// the error terms in |F| and |th| need, which leaves room for the three roundings
+// of the screen and for the 2^-23 |D| term; the frame's gscr = 2^-41 max_b
+// (|ih_b| + |nh_b|) covers the 2^-47 term 64 times over. Otherwise, and for
 // frames deeper than 22 levels, it returns kUndecided: the caller decides in
 // FP64 (side64), once per level for all the sides left open.
 constexpr uint32_t kUndecided = 2u;
 __device__ __forceinline__ uint32_t child_side(const Ray& r, int a, uint32_t cc, int lev, float th, float tl,
-                                               float margin_t) {
+                                               float base) {
     if (lev - r.f < kMaxFrameBits) {
         const uint32_t rel = cc & ((1u << (lev - r.f)) - 1u);
         const float Mp = small_uint_to_float(2u * rel + 1u) * pow2f(-(lev + 1 - r.f));
         if (is_zero(r, a)) {
-            const float dm = __fadd_rn(__fsub_rn(r.nh[a], Mp), r.nl[a]);
+            const float dm = __fadd_rn(__fsub_rn(r.il[a], Mp), r.ih[a]);
             if (fabsf(dm) > kEpsDF) return dm >= 0.0f;
         } else {
             const float F = __fadd_rn(__fmaf_rn(Mp, r.ih[a], r.nh[a]), __fmaf_rn(Mp, r.il[a], r.nl[a]));
             const float D = __fsub_rn(__fsub_rn(F, th), tl);
-            const float screen = __fmaf_rn(kEps21, __fadd_rn(fabsf(F), fabsf(th)),
-                                           __fmaf_rn(kEps42, __fadd_rn(fabsf(r.ih[a]), fabsf(r.nh[a])), margin_t));
-            if (fabsf(D) * kOneMinus20 > screen) return r.ih[a] > 0.0f ? (D <= 0.0f) : (D > 0.0f);
+            if (fabsf(D) > __fmaf_rn(kEps21, fabsf(F), base)) return r.ih[a] > 0.0f ? (D <= 0.0f) : (D > 0.0f);
         }
     }
     return kUndecided;
@@ -407,7 +416,7 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         }
         uint32_t b3[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) b3[a] = child_side(r, a, r.c[a], lev, 0.0f, 0.0f, 0.0f);
+        for (int a = 0; a < 3; ++a) b3[a] = child_side(r, a, r.c[a], lev, 0.0f, 0.0f, r.gscr);
         if (b3[0] == kUndecided || b3[1] == kUndecided || b3[2] == kUndecided) {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -460,7 +469,8 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     const float P2 = small_uint_to_float((r.c[2] & fmask) + ((r.dpos >> 2) & 1u)) * sc;
     // FP32 screen: F_a = fl(fl(P_a ih + nh) + fl(P_a il + nl)) is within 2^-23 |F_a| + 2^-47 (|ih| + |nh|)
     // of the exact crossing time. When the runner-up F_s exceeds the smallest F_b by more than
-    // 2^-22 (|F_s| + |F_b|) + 2^-41 max_a (|ih_a| + |nh_a|) (the frame's gscr), F_b's face is the exit face,
+    // 2^-22 (|F_s| + |F_b|) + 2^-41 max_a (|ih_a| + |nh_a|) (the frame's gscr, over the axes with d_a != 0; the
+    // others evaluate to kBigF exactly), F_b's face is the exit face,
     // at least 2^-44 (|ih_b| + |ih_s|) ahead of the others in double-float time: only its double-float
     // time is formed. Otherwise (the ray passes within about 2^-22 frame units of an edge of the leaf) the
     // face is chosen in FP64 from the exact planes.
@@ -469,9 +479,9 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     bool have64 = false;
     double te64 = 0.0;
     {
-        const float F0 = is_zero(r, 0) ? kBigF : __fadd_rn(__fmaf_rn(P0, r.ih[0], r.nh[0]), __fmaf_rn(P0, r.il[0], r.nl[0]));
-        const float F1 = is_zero(r, 1) ? kBigF : __fadd_rn(__fmaf_rn(P1, r.ih[1], r.nh[1]), __fmaf_rn(P1, r.il[1], r.nl[1]));
-        const float F2 = is_zero(r, 2) ? kBigF : __fadd_rn(__fmaf_rn(P2, r.ih[2], r.nh[2]), __fmaf_rn(P2, r.il[2], r.nl[2]));
+        const float F0 = __fadd_rn(__fmaf_rn(P0, r.ih[0], r.nh[0]), __fmaf_rn(P0, r.il[0], r.nl[0]));
+        const float F1 = __fadd_rn(__fmaf_rn(P1, r.ih[1], r.nh[1]), __fmaf_rn(P1, r.il[1], r.nl[1]));
+        const float F2 = __fadd_rn(__fmaf_rn(P2, r.ih[2], r.nh[2]), __fmaf_rn(P2, r.il[2], r.nl[2]));
         ax = 0;
         float Fb = F0;
         if (F1 < Fb) { ax = 1; Fb = F1; }
@@ -498,11 +508,13 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
     const uint32_t cold = pick(ax, r.c[0], r.c[1], r.c[2]);
     const uint32_t cn = up ? cold + 1u : cold - 1u;
     const int Lold = r.L;
+    float base_ax = 0.0f;  // the child-side screen's per-step term (see child_side), with margin 2^-44 |inv_ax|
     auto need64 = [&]() {
         if (!have64) {
             te64 = face_t64(r, T, ax, cold + up, Lold);
             have64 = true;
             split_local(r, te64, teh, tel);
+            base_ax = __fmaf_rn(kEps21, fabsf(teh), __fadd_rn(r.gscr, kEpsDF * fabsf(inv_ax)));
             r.k->n_f64 += 1;
         }
         return te64;
@@ -541,7 +553,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
         }
         int32_t slot = load_slot<kSmem>(T, P.smem_records, prec, kk);
         if (kCount) r.n_rec += 1;
-        const float margin_ax = kEpsDF * fabsf(inv_ax);
+        base_ax = __fmaf_rn(kEps21, fabsf(teh), __fadd_rn(r.gscr, kEpsDF * fabsf(inv_ax)));
         while (slot > 0) {
             // internal cell at level lv (record `slot`): choose its child at level lv + 1
             if (!kRopes) stk[lv] = slot;
@@ -556,7 +568,7 @@ __device__ bool ray_step(Ray& r, const MixedParams& P, double inv_extent, int32_
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
                     b3[a] = a == ax ? (up ? 0u : 1u)
-                                    : (fexit ? kUndecided : child_side(r, a, cc[a], lv, teh, tel, margin_ax));
+                                    : (fexit ? kUndecided : child_side(r, a, cc[a], lv, teh, tel, base_ax));
                 if (b3[0] == kUndecided || b3[1] == kUndecided || b3[2] == kUndecided) {
                     const double t64 = need64();
 #pragma unroll
@@ -679,7 +691,8 @@ __global__ void __launch_bounds__(kBlock, CANVOX_MIN_BLOCKS) mixed_kernel(MixedP
         do {
             if (alive) alive = ray_step<kSmem, kRopes, kCount>(r, P, inv_extent, stk);
             busy = __ballot_sync(kFull, alive);
-        } while (busy != 0u && (drained || __popc(busy) > P.refill));
+            // (refill 0, the default: run until every lane is done; the uniform test skips the count)
+        } while (busy != 0u && (drained || P.refill == 0 || __popc(busy) > P.refill));
     }
     const unsigned long long v[7] = {r.k->n_rays, r.k->n_steps, kCount ? r.n_reads : 0u, kCount ? r.n_leaf : 0u,
                                      kCount ? r.n_rec : 0u, r.k->n_f64, r.k->n_rebase};
