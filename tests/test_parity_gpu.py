@@ -184,6 +184,29 @@ def test_deep_embedding_mixed_passes_fp32_fails(level):
         assert max_err(img32, ref) > 1e-3   # canvas-coordinate FP32 drifts at this depth
 
 
+@pytest.mark.parametrize("level,frames", [(23, 20), (26, 3), (26, 22)])
+def test_axis_aligned_rays_in_deep_frames(level, frames):
+    """Rays with one or two zero direction components (the middle row and column of odd-sized views whose
+    forward axis is a canvas axis), eyes on the scene's cell planes, inside the scene embedded deep in a
+    40 km canvas: such an axis has no crossing time, and the ray's fixed coordinate on it decides every child
+    side on that axis through frame set-ups, rebases and descents (Sec. 6.2's cell-local frames)."""
+    cv, lo, s = _embedded_scene(level)
+    bg = (0.1, 0.2, 0.3, 1.0)
+    e1 = lo + np.array([0.5, 0.25, 1.7]) * s        # on the x mid-plane and a y quarter plane, looking down -z
+    e2 = lo + np.array([-0.6, 0.5, 0.375]) * s      # outside the scene, looking along +x through it
+    e3 = lo + np.array([0.1, 0.625, 0.5]) * s       # inside the scene, looking along +y
+    cams = synth.cameras_array([
+        synth.look_at_camera(e1, e1 - np.array([0.0, 0.0, 1.0]) * s, [0, 1, 0], 0.4, 9, 9, 0, bg),
+        synth.look_at_camera(e2, e2 + np.array([1.0, 0.0, 0.0]) * s, [0, 1, 0], 0.3, 7, 5, 81, bg),
+        synth.look_at_camera(e3, e3 + np.array([0.0, 1.0, 0.0]) * s, [0, 0, 1], 0.9, 11, 9, 81 + 35, bg)])
+    ref = oracle.render(cv, cams)
+    img, st = render(cv, cams, key=("deep", level), frame_levels=frames)
+    assert max_err(img, ref) <= TOL
+    assert st["status"] == 0 and st["rays"] == 81 + 35 + 99
+    img64, _ = render(cv, cams, key=("deep", level), precision=cx.PREC_FP64_LINKS)
+    assert max_err(img64, ref) <= 1e-6
+
+
 @pytest.mark.parametrize("frames,traversal", [(2, 0), (3, 1), (8, 0), (8, 1)])
 def test_small_frames_rebase_often(frames, traversal):
     """Frames only a few levels deep make nearly every descent and many crossings rebase the ray (FP64 frame
