@@ -24,7 +24,8 @@
 // the drift of Sec. 6.3 (e0 + 7.5 eps L) does not accumulate across frames:
 // on a frame exit to the coarsest frame that holds the new leaf, on a descent
 // more than K levels below the frame to the frame depth - K (the deepest one
-// the canvas can need), so that a ray entering a deep region rebases once.
+// the canvas can need), so that a ray entering a deep region rebases once; a
+// ray that starts at the eye's leaf takes that frame from the start.
 // inv_d and nod_f are each kept as two FP32 words. Decisions (which face of the
 // leaf the ray leaves by, which side of a mid-plane it is on) are screened in
 // plain FP32 with a proven margin, and taken in FP64 from the exact planes when
@@ -313,8 +314,8 @@ __device__ __forceinline__ uint32_t side64(const Ray& r, const Tree& T, int a, u
     return high64(r, a, M, t);
 }
 
-// Frame level for a leaf at level L that has descended past its frame: the level depth - K that holds the
-// canvas's deepest leaves within K levels, kept within [L - K, L].
+// Frame level for a leaf at level L that has descended past its frame, and for a ray's first frame at the eye's
+// leaf: the level depth - K that holds the canvas's deepest leaves within K levels, kept within [L - K, L].
 __device__ __forceinline__ int deep_frame(int L, int depth, int K) { return max(L - K, min(max(0, depth - K), L)); }
 
 // Start ray g of the launch. Returns true if it has a leaf to step from.
@@ -394,7 +395,9 @@ __device__ bool ray_init(Ray& r, const MixedParams& P, double inv_extent, unsign
         if (kCount) r.n_reads += r.L;
         if (kCount) r.n_leaf += (uint32_t)E.stored;
         r.steps = 1;
-        r.f = max(0, r.L - P.frame_levels);
+        // the frame a descent would settle in (depth - K, within [L - K, L]): rays that start in a deep subtree
+        // do not rebase again on their first descent past the eye's frame
+        r.f = deep_frame(r.L, T.depth, P.frame_levels);
         set_frame(r, T, inv_extent, t0);
         return true;
     }
