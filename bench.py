@@ -91,8 +91,10 @@ def profiled_counters(cid, res_scale, n_fine):
                 fields[k.strip()] = v.strip()
     if fields.get("kernel_sha256") != sha:
         return None
-    return {k: float(fields[k]) for k in ("dram_bytes_per_launch", "lts_bytes_per_launch", "warp_inst_per_launch",
-                                          "thread_inst_per_launch", "steps_per_launch")}
+    ctr = {k: float(fields[k]) for k in ("dram_bytes_per_launch", "lts_bytes_per_launch", "warp_inst_per_launch",
+                                         "thread_inst_per_launch", "steps_per_launch")}
+    ctr["stalls"] = {k[len("stall_share_"):]: float(v) for k, v in fields.items() if k.startswith("stall_share_")}
+    return ctr
 
 
 class Clocks:
@@ -442,6 +444,11 @@ def main():
                 "warp_inst_per_leaf_step": ctr["warp_inst_per_launch"] / ctr["steps_per_launch"]}
             roofline["l2"] = {"achieved": ctr["lts_bytes_per_launch"] / (ms_step * 1e-3) / 1e9, "unit": "GB/s",
                               "note": "lts__t_bytes per launch (ncu) over the timed launch; see l2_gather for the probe"}
+            if ctr["stalls"]:
+                roofline["stalls"] = {
+                    "memory_latency": ctr["stalls"].get("long_scoreboard"), "share_of_stall_cycles": ctr["stalls"],
+                    "note": "ncu stall reasons of the same kernel source on the reduced stereo case (--set full); "
+                            "memory_latency = long scoreboard (L1/L2 gathers, spilled words)"}
         line = {
             "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
