@@ -26,7 +26,9 @@
 // per refined cell classifies that list against its eight children, 32
 // entries at a time (a cell around a room holds tens of thousands of stamps),
 // with each stamp's distances to the cell's three planes per axis shared by
-// the children. Geometry is FP64 with the
+// the children. Levels of few cells take a warp per child instead, and, where
+// the lists run long (near the root every stamp is on them), a warp per chunk
+// of a child's list. Geometry is FP64 with the
 // same operations and order as the host painter, so the pools are identical.
 #include <algorithm>
 #include <cmath>
@@ -592,6 +594,208 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_child_write(LevelI
     }
 }
 
+// The per-child passes once more, for the few cells near the root whose lists hold most of the stamp table: a
+// child's list is cut into chunks of kChunk entries, one warp each, so that the level runs on thousands of warps
+// instead of eight. The first refining stamp is the least one any chunk finds (entries are in stamp order), the
+// kept entries are counted per chunk and written at the chunk's place in an exclusive scan over the chunks (which
+// keeps every next-level list in stamp order), and a child that stays a leaf blends its painting stamps in order
+// in one warp (near the root such children have none, and skip it). Every per-entry decision is the one of the
+// passes above, so the pools are the same.
+constexpr int64_t kChunk = 2048;         // entries per warp
+constexpr int64_t kChunkMinList = 8192;  // a level whose longest list is longer takes the chunked passes
+constexpr int32_t kNoStamp = 0x7FFFFFFF;
+
+struct ChunkWork {
+    int64_t t;      // child 8 i + k of refined cell i
+    int64_t b, e;   // its entries [b, e) of cell i's list
+    int32_t first;  // 1 for the child's first chunk
+};
+
+// Whether list entry v (a stamp that still descends) partially covers child k and has its target below level lc.
+__device__ __forceinline__ bool refines_child(const StampDev& S, int32_t v, int k, int lc, const double pl[3],
+                                              const double pm[3], const double pu[3], const double cl[3],
+                                              const double cm[3], float hf, float hhf) {
+    if (v < 0 || S.kt[v] <= lc) return false;
+    const double r2 = S.r2[v];
+    FastTerms F;
+    fast_terms(S.c + 3 * (int64_t)v, pl, hf, hhf, r2, F);
+    const int f = partial_fast(F, k);
+    if (f >= 0) return f == 1;
+    ParentTerms T;
+    parent_terms(S.c + 3 * (int64_t)v, pl, pm, pu, cl, cm, T);
+    const double dmin2 = __dadd_rn(__dadd_rn(half_term(T.dmin, k, 0), half_term(T.dmin, k, 1)), half_term(T.dmin, k, 2));
+    const double dmax2 = __dadd_rn(__dadd_rn(half_term(T.dmax, k, 0), half_term(T.dmax, k, 1)), half_term(T.dmax, k, 2));
+    return dmin2 < r2 && dmax2 > r2;
+}
+
+// kDrop / kPaint / kKeep of list entry x for child k whose first refining stamp is fr (kNoStamp: none).
+__device__ __forceinline__ int entry_class(const StampDev& S, int32_t x, int k, int32_t fr, const double pl[3],
+                                           const double pm[3], const double pu[3], const double cl[3],
+                                           const double cm[3], float hf, float hhf) {
+    if (x < 0) return kPaint;
+    const double r2 = S.r2[x];
+    FastTerms F;
+    fast_terms(S.c + 3 * (int64_t)x, pl, hf, hhf, r2, F);
+    return child_class(S, F, x, r2, k, fr != kNoStamp && fr <= x, pl, pm, pu, cl, cm);
+}
+
+__global__ void chunk_init(int64_t nch, int32_t* fr, int64_t* cnt, int64_t* npaint) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nch) return;
+    fr[t] = kNoStamp;
+    cnt[t] = 0;
+    npaint[t] = 0;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_firstref(LevelIn L, StampDev S, int32_t depth, double extent,
+                                                                      double half, const ChunkWork* W, int64_t nw,
+                                                                      int32_t* fr) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int lc = L.level + 1;
+    if (w >= nw || lc >= depth) return;  // warp-uniform
+    const ChunkWork cw = W[w];
+    const int k = (int)(cw.t & 7);
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, cw.t >> 3, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
+    for (int64_t base = cw.b; base < cw.e; base += 32) {
+        const int64_t q = base + lane;
+        const int32_t v = q < cw.e ? L.ent[q] : -1;
+        const unsigned m = __ballot_sync(kFullMask, refines_child(S, v, k, lc, pl, pm, pu, cl, cm, hf, hhf));
+        if (m) {
+            const int32_t first = __shfl_sync(kFullMask, v, __ffs(m) - 1);
+            if (lane == 0) atomicMin(&fr[cw.t], first);
+            break;
+        }
+    }
+}
+
+// Per chunk: the entries a refined child keeps (chunk_cnt, summed into cnt), or the ones that paint a child that
+// stays a leaf (summed into npaint).
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_count(LevelIn L, StampDev S, double extent, double half,
+                                                                   const ChunkWork* W, int64_t nw, const int32_t* fr,
+                                                                   int64_t* chunk_cnt, int64_t* cnt, int64_t* npaint) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nw) return;
+    const ChunkWork cw = W[w];
+    const int k = (int)(cw.t & 7);
+    const int32_t f = fr[cw.t];
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, cw.t >> 3, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
+    int64_t n = 0;
+    for (int64_t base = cw.b; base < cw.e; base += 32) {
+        const int64_t q = base + lane;
+        const int c = q < cw.e ? entry_class(S, L.ent[q], k, f, pl, pm, pu, cl, cm, hf, hhf) : kDrop;
+        n += __popc(__ballot_sync(kFullMask, f != kNoStamp ? c != kDrop : c == kPaint));
+    }
+    if (lane == 0) {
+        chunk_cnt[w] = f != kNoStamp ? n : 0;
+        if (n)
+            atomicAdd(reinterpret_cast<unsigned long long*>(f != kNoStamp ? &cnt[cw.t] : &npaint[cw.t]),
+                      (unsigned long long)n);
+    }
+}
+
+// Per child: an internal slot, or the leaf key of the blend, in stamp order, of the stamps that paint it.
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_child_finish(LevelIn L, StampDev S, double extent, double half,
+                                                                          const int32_t* fr, const int64_t* npaint,
+                                                                          uint64_t* slot, int64_t* cnt, int64_t* is_int) {
+    __shared__ int32_t s_idx[kWarpsPerBlock][32];
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (t >= 8 * L.n) return;  // warp-uniform
+    if (fr[t] != kNoStamp) {
+        if (lane == 0) {
+            is_int[t] = 1;
+            slot[t] = kInternal;
+        }
+        return;
+    }
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (npaint[t] > 0) {
+        const int64_t i = t >> 3;
+        const int k = (int)(t & 7);
+        double pl[3], pm[3], pu[3], cl[3], cm[3];
+        parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
+        const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
+        const int64_t b = L.off[i], e = L.off[i + 1];
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t q = base + lane;
+            int32_t x = 0;
+            int c = kDrop;
+            if (q < e) {
+                x = L.ent[q];
+                c = entry_class(S, x, k, kNoStamp, pl, pm, pu, cl, cm, hf, hhf);
+            }
+            s_idx[wib][lane] = x < 0 ? ~x : x;
+            unsigned m = __ballot_sync(kFullMask, c == kPaint);
+            __syncwarp();
+            while (m) {  // every lane folds the same sequence
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                blend(val, S.rgba[s_idx[wib][j]]);
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        cnt[t] = 0;
+        is_int[t] = 0;
+        slot[t] = leaf_key(val);
+    }
+}
+
+// Per chunk of a refined child: its kept entries at the chunk's place in the next level's lists (chunk_off, the
+// exclusive scan of chunk_cnt); the child's first chunk also writes its cell and list start.
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_write(LevelIn L, StampDev S, double extent, double half,
+                                                                   const ChunkWork* W, int64_t nw, const int32_t* fr,
+                                                                   uint64_t* slot, const int64_t* ent_off,
+                                                                   const int64_t* next_idx, const int64_t* chunk_off,
+                                                                   uint32_t* ncoord, int64_t* noff, int32_t* nent) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nw) return;
+    const ChunkWork cw = W[w];
+    const int32_t f = fr[cw.t];
+    if (f == kNoStamp) return;  // a leaf child
+    const int64_t i = cw.t >> 3;
+    const int k = (int)(cw.t & 7);
+    if (cw.first && lane == 0) {
+        const int64_t j = next_idx[cw.t];
+        slot[cw.t] = kInternal | (uint64_t)j;
+        ncoord[3 * j] = 2u * L.coord[3 * i] + (k & 1u);
+        ncoord[3 * j + 1] = 2u * L.coord[3 * i + 1] + ((k >> 1) & 1u);
+        ncoord[3 * j + 2] = 2u * L.coord[3 * i + 2] + ((k >> 2) & 1u);
+        noff[j] = ent_off[cw.t];
+    }
+    double pl[3], pm[3], pu[3], cl[3], cm[3];
+    parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
+    const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
+    int64_t pos = chunk_off[w];
+    for (int64_t base = cw.b; base < cw.e; base += 32) {
+        const int64_t q = base + lane;
+        int32_t out = 0;
+        bool keep = false;
+        if (q < cw.e) {
+            const int32_t x = L.ent[q];
+            if (x < 0) {
+                out = x;
+                keep = true;
+            } else {
+                const int c = entry_class(S, x, k, f, pl, pm, pu, cl, cm, hf, hhf);
+                keep = c != kDrop;
+                out = c == kPaint ? ~x : x;
+            }
+        }
+        const unsigned m = __ballot_sync(kFullMask, keep);
+        if (keep) nent[pos + __popc(m & ((1u << lane) - 1u))] = out;
+        pos += __popc(m);
+    }
+}
+
 // Stamps that touch the canvas, in order (the root's list).
 __global__ void root_flags(StampDev S, int64_t n, double extent, double half, int64_t* flag) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1002,6 +1206,23 @@ cudaError_t dalloc(T** p, int64_t n) {
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
 }
 
+// Chunks of the per-child passes for a level of few cells (see chunk_firstref): none when its longest list is
+// short enough for a warp per child.
+cudaError_t chunk_plan(const Level& L, std::vector<ChunkWork>* work) {
+    work->clear();
+    std::vector<int64_t> off((size_t)L.n + 1);
+    const cudaError_t e = cudaMemcpy(off.data(), L.off, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    int64_t longest = 0;
+    for (int64_t i = 0; i < L.n; ++i) longest = std::max(longest, off[(size_t)i + 1] - off[(size_t)i]);
+    if (longest <= kChunkMinList) return cudaSuccess;
+    for (int64_t i = 0; i < L.n; ++i)
+        for (int k = 0; k < 8; ++k)
+            for (int64_t b = off[(size_t)i]; b < off[(size_t)i + 1]; b += kChunk)
+                work->push_back(ChunkWork{8 * i + k, b, std::min(off[(size_t)i + 1], b + kChunk), b == off[(size_t)i] ? 1 : 0});
+    return cudaSuccess;
+}
+
 // Expand one level: the eight child slots of each cell (*slot_out, handed to the caller: a leaf key, or
 // kInternal | index in the next level) and the next level's refined cells with their lists.
 cudaError_t expand(const Level& L, const StampDev& S, int32_t depth, double extent, double half, uint64_t** slot_out,
@@ -1018,7 +1239,23 @@ cudaError_t expand(const Level& L, const StampDev& S, int32_t depth, double exte
     *slot_out = slot;
     const LevelIn in = L.in();
     const bool split = L.n < kSplitCells;  // few cells: a warp per child
-    if (split)
+    std::vector<ChunkWork> work;
+    if (split) PCK(chunk_plan(L, &work));  // and, for long lists, a warp per chunk of a child's list
+    const int64_t nw = (int64_t)work.size();
+    ChunkWork* d_work = nullptr;
+    int64_t *chunk_cnt = nullptr, *npaint = nullptr;
+    if (nw) {
+        PCK(buf.alloc(&d_work, nw));
+        PCK(buf.alloc(&chunk_cnt, nw));
+        PCK(buf.alloc(&npaint, nch));
+        PCK(cudaMemcpy(d_work, work.data(), sizeof(ChunkWork) * (size_t)nw, cudaMemcpyHostToDevice));
+        chunk_init<<<blocks_for(nch, 256), 256>>>(nch, fr, cnt, npaint);
+        chunk_firstref<<<blocks_for(nw, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, d_work, nw, fr);
+        chunk_count<<<blocks_for(nw, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, d_work, nw, fr, chunk_cnt,
+                                                                             cnt, npaint);
+        chunk_child_finish<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, npaint, slot,
+                                                                                    cnt, isint);
+    } else if (split)
         expand_child_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, fr, slot,
                                                                                     cnt, isint);
     else
@@ -1035,7 +1272,13 @@ cudaError_t expand(const Level& L, const StampDev& S, int32_t depth, double exte
     PCK(dalloc(&next->off, n_next + 1));
     PCK(dalloc(&next->ent, n_ent));
     PCK(cudaMemcpy(next->off + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
-    if (split)
+    if (nw) {
+        int64_t n_chunked = 0;
+        PCK(scan_i64(chunk_cnt, nw, &n_chunked));  // the same total as n_ent, in the same order
+        chunk_write<<<blocks_for(nw, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, d_work, nw, fr, slot, cnt,
+                                                                             isint, chunk_cnt, next->coord, next->off,
+                                                                             next->ent);
+    } else if (split)
         expand_child_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, slot, cnt,
                                                                                     isint, next->coord, next->off,
                                                                                     next->ent);

@@ -59,6 +59,37 @@ def test_paint_random_stamps(seed, D):
     _paint_and_compare(D, E, c, r, q)
 
 
+def test_paint_long_lists_near_the_root():
+    """More than 8192 stamps in the root's list, so the top levels take the chunked per-child passes: lists cut
+    into chunks of 2048, a child painted whole by stamps spread through the order that stays a leaf (the in-order
+    blend), a whole-canvas stamp halfway through, children with few or no stamps; then an append of stamps into the
+    painted octant, which refines it."""
+    rng = np.random.default_rng(17)
+    D, E = 10, 1000.0
+    n_small = 15000
+    cs = rng.uniform(-0.5, -0.25, (n_small, 3)) * E            # small stamps in one corner of one octant
+    rs = E * np.exp(rng.uniform(math.log(2.0 ** -11), math.log(0.02), n_small))
+    cb = np.tile([0.25 * E, 0.25 * E, 0.25 * E], (30, 1))
+    rb = np.full(30, 0.45 * E)                                    # each covers the whole octant x, y, z > 0
+    c = np.concatenate([cs, cb])
+    r = np.concatenate([rs, rb])
+    order = rng.permutation(len(r))
+    c, r = c[order], r[order]
+    q = np.c_[rng.uniform(0, 1, (len(r), 3)), rng.uniform(0, 30, len(r))].astype(np.float32)
+    mid = len(r) // 2
+    c[mid] = (0.0, 0.0, 0.0)
+    r[mid] = 2.0 * E                                              # the whole canvas
+    _paint_and_compare(D, E, c, r, q)
+    ca = rng.uniform(0.05, 0.45, (200, 3)) * E
+    ra = E * np.exp(rng.uniform(math.log(2.0 ** -10), math.log(0.01), 200))
+    qa = np.c_[rng.uniform(0, 1, (200, 3)), rng.uniform(0, 30, 200)].astype(np.float32)
+    ref = synth.stamp_canvas(D, E, np.concatenate([c, ca]), np.concatenate([r, ra]), np.concatenate([q, qa]))
+    cx.paint_append(ca, ra, qa)
+    nodes, leaves = cx.download_octree()
+    np.testing.assert_array_equal(nodes, ref.nodes)
+    np.testing.assert_array_equal(leaves, ref.leaves)
+
+
 def test_paint_empty_and_deep_reduced_c2():
     _paint_and_compare(4, 1.0, np.zeros((0, 3)), np.zeros(0), np.zeros((0, 4), np.float32))
     D, E, c, r, q, _ = synth.config_stamps(2, n_fine=4000)
