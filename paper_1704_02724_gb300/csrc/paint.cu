@@ -26,9 +26,9 @@
 // per refined cell classifies that list against its eight children, 32
 // entries at a time (a cell around a room holds tens of thousands of stamps),
 // with each stamp's distances to the cell's three planes per axis shared by
-// the children. Levels of few cells take a warp per child instead, and, where
-// the lists run long (near the root every stamp is on them), a warp per chunk
-// of a child's list. Geometry is FP64 with the
+// the children. Levels of few cells take a warp per child instead, and cells
+// whose lists run long (near the root every stamp is on them; around a room,
+// its stamps) a warp per chunk of a child's list. Geometry is FP64 with the
 // same operations and order as the host painter, so the pools are identical.
 #include <algorithm>
 #include <cmath>
@@ -218,11 +218,12 @@ __device__ __forceinline__ void parent_planes(const LevelIn& L, int64_t i, doubl
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_count(LevelIn L, StampDev S, int32_t depth,
                                                                            double extent, double half, int32_t* firstref,
-                                                                           uint64_t* slot, int64_t* count, int64_t* is_int) {
+                                                                           uint64_t* slot, int64_t* count, int64_t* is_int,
+                                                                           const uint8_t* skip) {
     __shared__ int32_t s_idx[kWarpsPerBlock][32];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (i >= L.n) return;  // warp-uniform
+    if (i >= L.n || (skip && skip[i])) return;  // warp-uniform (skipped cells take the chunked passes)
     double pl[3], pm[3], pu[3], cl[3], cm[3];
     parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
     const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;  // child side and half side (exact)
@@ -356,10 +357,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_parent_write(Level
                                                                            double half, const int32_t* firstref,
                                                                            uint64_t* slot, const int64_t* ent_off,
                                                                            const int64_t* next_idx, uint32_t* ncoord,
-                                                                           int64_t* noff, int32_t* nent) {
+                                                                           int64_t* noff, int32_t* nent, const uint8_t* skip) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= L.n) return;
+    if (i >= L.n || (skip && skip[i])) return;
     int32_t fr[8];
     int64_t w[8];
     unsigned internal = 0;
@@ -454,11 +455,12 @@ __device__ __forceinline__ int child_class(const StampDev& S, const FastTerms& F
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_child_count(LevelIn L, StampDev S, int32_t depth,
                                                                           double extent, double half, int32_t* firstref,
-                                                                          uint64_t* slot, int64_t* count, int64_t* is_int) {
+                                                                          uint64_t* slot, int64_t* count, int64_t* is_int,
+                                                                          const uint8_t* skip) {
     __shared__ int32_t s_idx[kWarpsPerBlock][32];
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (t >= 8 * L.n) return;  // warp-uniform
+    if (t >= 8 * L.n || (skip && skip[t >> 3])) return;  // warp-uniform
     const int64_t i = t >> 3;
     const int k = (int)(t & 7);
     double pl[3], pm[3], pu[3], cl[3], cm[3];
@@ -548,10 +550,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_child_write(LevelI
                                                                           double half, const int32_t* firstref,
                                                                           uint64_t* slot, const int64_t* ent_off,
                                                                           const int64_t* next_idx, uint32_t* ncoord,
-                                                                          int64_t* noff, int32_t* nent) {
+                                                                          int64_t* noff, int32_t* nent, const uint8_t* skip) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (t >= 8 * L.n) return;
+    if (t >= 8 * L.n || (skip && skip[t >> 3])) return;
     if (slot[t] != kInternal) return;  // warp-uniform
     const int64_t i = t >> 3;
     const int k = (int)(t & 7);
@@ -594,20 +596,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) expand_child_write(LevelI
     }
 }
 
-// The per-child passes once more, for the few cells near the root whose lists hold most of the stamp table: a
-// child's list is cut into chunks of kChunk entries, one warp each, so that the level runs on thousands of warps
-// instead of eight. The first refining stamp is the least one any chunk finds (entries are in stamp order), the
-// kept entries are counted per chunk and written at the chunk's place in an exclusive scan over the chunks (which
-// keeps every next-level list in stamp order), and a child that stays a leaf blends its painting stamps in order
-// in one warp (near the root such children have none, and skip it). Every per-entry decision is the one of the
-// passes above, so the pools are the same.
+// The per-child passes once more, for the cells whose lists are long (near the root every stamp is on them, and
+// around a room its tens of thousands of stamps are, level after level): a child's list is cut into chunks of
+// kChunk entries, one warp each, so that such a cell runs on hundreds of warps instead of one (or eight). The
+// first refining stamp is the least one any chunk finds (entries are in stamp order), the kept entries are counted
+// per chunk and written at the child's list start plus the counts of its earlier chunks (which keeps every
+// next-level list in stamp order), and a child that stays a leaf blends its painting stamps in order in one warp
+// (such children of long lists rarely have any, and skip it). Every per-entry decision is the one of the passes
+// above, so the pools are the same. The level's other cells take those passes, which skip the long ones.
 constexpr int64_t kChunk = 2048;         // entries per warp
-constexpr int64_t kChunkMinList = 8192;  // a level whose longest list is longer takes the chunked passes
+constexpr int64_t kChunkMinList = 8192;  // cells whose list is longer take the chunked passes
 constexpr int32_t kNoStamp = 0x7FFFFFFF;
 
 struct ChunkWork {
     int64_t t;      // child 8 i + k of refined cell i
     int64_t b, e;   // its entries [b, e) of cell i's list
+    int64_t fw;     // index of the child's first chunk
     int32_t first;  // 1 for the child's first chunk
 };
 
@@ -639,9 +643,30 @@ __device__ __forceinline__ int entry_class(const StampDev& S, int32_t x, int k, 
     return child_class(S, F, x, r2, k, fr != kNoStamp && fr <= x, pl, pm, pu, cl, cm);
 }
 
-__global__ void chunk_init(int64_t nch, int32_t* fr, int64_t* cnt, int64_t* npaint) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nch) return;
+// Cells with lists longer than kChunkMinList: skip[i] = flag[i] = 1.
+__global__ void flag_long(LevelIn L, uint8_t* skip, int64_t* flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const bool lg = L.off[i + 1] - L.off[i] > kChunkMinList;
+    skip[i] = lg ? 1 : 0;
+    flag[i] = lg ? 1 : 0;
+}
+
+// The long cells in order, as (cell, list start, list end); pos = exclusive scan of their flags.
+__global__ void gather_long(LevelIn L, const uint8_t* skip, const int64_t* pos, int64_t* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n || !skip[i]) return;
+    const int64_t j = pos[i];
+    out[3 * j] = i;
+    out[3 * j + 1] = L.off[i];
+    out[3 * j + 2] = L.off[i + 1];
+}
+
+// Children of the long cells: cells[j >> 3] is the cell of the j-th.
+__global__ void chunk_init(const int64_t* cells, int64_t nj, int32_t* fr, int64_t* cnt, int64_t* npaint) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nj) return;
+    const int64_t t = 8 * cells[j >> 3] + (j & 7);
     fr[t] = kNoStamp;
     cnt[t] = 0;
     npaint[t] = 0;
@@ -701,12 +726,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_count(LevelIn L, St
 
 // Per child: an internal slot, or the leaf key of the blend, in stamp order, of the stamps that paint it.
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_child_finish(LevelIn L, StampDev S, double extent, double half,
+                                                                          const int64_t* cells, int64_t nj,
                                                                           const int32_t* fr, const int64_t* npaint,
                                                                           uint64_t* slot, int64_t* cnt, int64_t* is_int) {
     __shared__ int32_t s_idx[kWarpsPerBlock][32];
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t jj = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (t >= 8 * L.n) return;  // warp-uniform
+    if (jj >= nj) return;  // warp-uniform
+    const int64_t t = 8 * cells[jj >> 3] + (jj & 7);
     if (fr[t] != kNoStamp) {
         if (lane == 0) {
             is_int[t] = 1;
@@ -748,12 +775,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_child_finish(LevelI
     }
 }
 
-// Per chunk of a refined child: its kept entries at the chunk's place in the next level's lists (chunk_off, the
-// exclusive scan of chunk_cnt); the child's first chunk also writes its cell and list start.
+// Per chunk of a refined child: its kept entries at the child's list start plus the kept entries of its earlier
+// chunks (chunk_scan, the exclusive scan of chunk_cnt over all chunks); the child's first chunk also writes its
+// cell and list start.
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_write(LevelIn L, StampDev S, double extent, double half,
                                                                    const ChunkWork* W, int64_t nw, const int32_t* fr,
                                                                    uint64_t* slot, const int64_t* ent_off,
-                                                                   const int64_t* next_idx, const int64_t* chunk_off,
+                                                                   const int64_t* next_idx, const int64_t* chunk_scan,
                                                                    uint32_t* ncoord, int64_t* noff, int32_t* nent) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -774,7 +802,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) chunk_write(LevelIn L, St
     double pl[3], pm[3], pu[3], cl[3], cm[3];
     parent_planes(L, i, extent, half, pl, pm, pu, cl, cm);
     const float hf = (float)(pm[0] - pl[0]), hhf = 0.5f * hf;
-    int64_t pos = chunk_off[w];
+    int64_t pos = ent_off[cw.t] + (chunk_scan[w] - chunk_scan[cw.fw]);
     for (int64_t base = cw.b; base < cw.e; base += 32) {
         const int64_t q = base + lane;
         int32_t out = 0;
@@ -1206,20 +1234,39 @@ cudaError_t dalloc(T** p, int64_t n) {
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
 }
 
-// Chunks of the per-child passes for a level of few cells (see chunk_firstref): none when its longest list is
-// short enough for a warp per child.
-cudaError_t chunk_plan(const Level& L, std::vector<ChunkWork>* work) {
+// The long cells of a level (lists longer than kChunkMinList) and the chunks of their children's lists (see
+// chunk_firstref); *skip marks them for the level's other passes. Nothing when the level has none.
+cudaError_t chunk_plan(const Level& L, DevBuf& buf, uint8_t** skip, std::vector<int64_t>* cells,
+                       std::vector<ChunkWork>* work) {
+    *skip = nullptr;
+    cells->clear();
     work->clear();
-    std::vector<int64_t> off((size_t)L.n + 1);
-    const cudaError_t e = cudaMemcpy(off.data(), L.off, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    int64_t longest = 0;
-    for (int64_t i = 0; i < L.n; ++i) longest = std::max(longest, off[(size_t)i + 1] - off[(size_t)i]);
-    if (longest <= kChunkMinList) return cudaSuccess;
-    for (int64_t i = 0; i < L.n; ++i)
-        for (int k = 0; k < 8; ++k)
-            for (int64_t b = off[(size_t)i]; b < off[(size_t)i + 1]; b += kChunk)
-                work->push_back(ChunkWork{8 * i + k, b, std::min(off[(size_t)i + 1], b + kChunk), b == off[(size_t)i] ? 1 : 0});
+    int64_t total = 0;  // entries of the whole level: no cell is long if they are few
+    cudaError_t e = cudaMemcpy(&total, L.off + L.n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess || total <= kChunkMinList) return e;
+    uint8_t* sk = nullptr;
+    int64_t *flag = nullptr, *out = nullptr;
+    if ((e = buf.alloc(&sk, L.n)) != cudaSuccess || (e = buf.alloc(&flag, L.n)) != cudaSuccess) return e;
+    flag_long<<<blocks_for(L.n, 256), 256>>>(L.in(), sk, flag);
+    int64_t n_long = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = scan_i64(flag, L.n, &n_long)) != cudaSuccess) return e;
+    if (n_long == 0) return cudaSuccess;
+    if ((e = buf.alloc(&out, 3 * n_long)) != cudaSuccess) return e;
+    gather_long<<<blocks_for(L.n, 256), 256>>>(L.in(), sk, flag, out);
+    std::vector<int64_t> h((size_t)(3 * n_long));
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpy(h.data(), out, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    for (int64_t j = 0; j < n_long; ++j) {
+        const int64_t i = h[(size_t)(3 * j)], b0 = h[(size_t)(3 * j + 1)], e0 = h[(size_t)(3 * j + 2)];
+        cells->push_back(i);
+        for (int k = 0; k < 8; ++k) {
+            const int64_t fw = (int64_t)work->size();
+            for (int64_t b = b0; b < e0; b += kChunk)
+                work->push_back(ChunkWork{8 * i + k, b, std::min(e0, b + kChunk), fw, b == b0 ? 1 : 0});
+        }
+    }
+    *skip = sk;
     return cudaSuccess;
 }
 
@@ -1239,28 +1286,34 @@ cudaError_t expand(const Level& L, const StampDev& S, int32_t depth, double exte
     *slot_out = slot;
     const LevelIn in = L.in();
     const bool split = L.n < kSplitCells;  // few cells: a warp per child
+    // cells with long lists: a warp per chunk of a child's list (the passes below skip them)
+    uint8_t* skip = nullptr;
+    std::vector<int64_t> cells;
     std::vector<ChunkWork> work;
-    if (split) PCK(chunk_plan(L, &work));  // and, for long lists, a warp per chunk of a child's list
-    const int64_t nw = (int64_t)work.size();
+    PCK(chunk_plan(L, buf, &skip, &cells, &work));
+    const int64_t nw = (int64_t)work.size(), nj = 8 * (int64_t)cells.size();
     ChunkWork* d_work = nullptr;
-    int64_t *chunk_cnt = nullptr, *npaint = nullptr;
+    int64_t *d_cells = nullptr, *chunk_cnt = nullptr, *npaint = nullptr;
     if (nw) {
         PCK(buf.alloc(&d_work, nw));
+        PCK(buf.alloc(&d_cells, (int64_t)cells.size()));
         PCK(buf.alloc(&chunk_cnt, nw));
         PCK(buf.alloc(&npaint, nch));
         PCK(cudaMemcpy(d_work, work.data(), sizeof(ChunkWork) * (size_t)nw, cudaMemcpyHostToDevice));
-        chunk_init<<<blocks_for(nch, 256), 256>>>(nch, fr, cnt, npaint);
+        PCK(cudaMemcpy(d_cells, cells.data(), sizeof(int64_t) * cells.size(), cudaMemcpyHostToDevice));
+        chunk_init<<<blocks_for(nj, 256), 256>>>(d_cells, nj, fr, cnt, npaint);
         chunk_firstref<<<blocks_for(nw, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, d_work, nw, fr);
         chunk_count<<<blocks_for(nw, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, d_work, nw, fr, chunk_cnt,
                                                                              cnt, npaint);
-        chunk_child_finish<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, npaint, slot,
-                                                                                    cnt, isint);
-    } else if (split)
+        chunk_child_finish<<<blocks_for(nj, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, d_cells, nj, fr,
+                                                                                   npaint, slot, cnt, isint);
+    }
+    if (split)
         expand_child_count<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, fr, slot,
-                                                                                    cnt, isint);
+                                                                                    cnt, isint, skip);
     else
         expand_parent_count<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, depth, extent, half, fr,
-                                                                                     slot, cnt, isint);
+                                                                                     slot, cnt, isint, skip);
     PCK(cudaGetLastError());
     int64_t n_ent = 0, n_next = 0;
     PCK(scan_i64(cnt, nch, &n_ent));
@@ -1274,18 +1327,19 @@ cudaError_t expand(const Level& L, const StampDev& S, int32_t depth, double exte
     PCK(cudaMemcpy(next->off + n_next, &n_ent, sizeof(int64_t), cudaMemcpyHostToDevice));
     if (nw) {
         int64_t n_chunked = 0;
-        PCK(scan_i64(chunk_cnt, nw, &n_chunked));  // the same total as n_ent, in the same order
+        PCK(scan_i64(chunk_cnt, nw, &n_chunked));  // per child: its list start plus the counts of earlier chunks
         chunk_write<<<blocks_for(nw, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, d_work, nw, fr, slot, cnt,
                                                                              isint, chunk_cnt, next->coord, next->off,
                                                                              next->ent);
-    } else if (split)
+    }
+    if (split)
         expand_child_write<<<blocks_for(nch, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, slot, cnt,
                                                                                     isint, next->coord, next->off,
-                                                                                    next->ent);
+                                                                                    next->ent, skip);
     else
         expand_parent_write<<<blocks_for(L.n, kWarpsPerBlock), 32 * kWarpsPerBlock>>>(in, S, extent, half, fr, slot,
                                                                                      cnt, isint, next->coord, next->off,
-                                                                                     next->ent);
+                                                                                     next->ent, skip);
     PCK(cudaGetLastError());
     return cudaDeviceSynchronize();
 }
