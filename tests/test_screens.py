@@ -196,3 +196,32 @@ def test_zero_direction_axis_time_is_exactly_big():
         P = dyadic_plane(rng, rng.randint(0, 22))
         hi, lo = split(Q(rng.uniform(-1.0, 2.0)))
         assert add(fma(P, lo, BIG), fma(P, hi, Q(0))) == BIG
+
+
+def df_cross(P, ih, il, nh, nl):
+    """The kernel's double-float crossing time P (ih + il) + (nh + nl): the product error by one fma (Dekker), the
+    sum error by Knuth's two-sum, the low terms in one fma, then a fast two-sum into hi + lo."""
+    p = mul(P, ih)
+    pe = fma(P, ih, -p)
+    s = add(p, nh)
+    v = sub(s, p)
+    se = add(sub(p, sub(s, v)), sub(nh, v))
+    t = add(add(pe, se), fma(P, il, nl))
+    hi = add(s, t)
+    return hi, sub(t, sub(hi, s))
+
+
+def test_double_float_crossing_time_bound():
+    """hi + lo is within 2^-44 |ih| of the exact P (ih + il) + (nh + nl) for planes P in [0, 1] of a frame and
+    frame-local offsets |nod| up to 3 |inv|: the bound the screens allow the exit time."""
+    rng = random.Random(13)
+    worst = Q(0)
+    for _ in range(4000):
+        ih, il, nh, nl, _ = frame(rng)
+        a = rng.randrange(3)
+        P = dyadic_plane(rng, rng.randint(0, 22))
+        hi, lo = df_cross(P, ih[a], il[a], nh[a], nl[a])
+        err = abs(hi + lo - (P * (ih[a] + il[a]) + nh[a] + nl[a])) / abs(ih[a])
+        worst = max(worst, err)
+        assert err <= EPS44
+    assert worst > 0   # not exact by accident: the bound is exercised
