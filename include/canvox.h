@@ -268,7 +268,9 @@ int canvox_render_host(const canvox_camera* cams, int32_t n_views, float* out_rg
  * The working memory (counters, ray-queue head, view table, eye paths) is one
  * fixed 24 KiB array in device global memory that every GPU loading the
  * library holds until the process exits. The first call on a device looks up
- * that array's device address, so make it before any stream capture. All
+ * that array's device address and keeps it, so make it before any stream
+ * capture, and do not reset the device (cudaDeviceReset) between calls in one
+ * process: the kept address would then be stale. All
  * calls share the array: calls that overlap on the GPU race, so serialise
  * them (one stream, or wait between them). Each call first clears the
  * array's counters and queue head and stores its view table there with a
